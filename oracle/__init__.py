@@ -1,0 +1,180 @@
+"""Oracle for Dykstra's method on the regularized correlation-clustering LP.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline / reference legs may import this package.  The
+product path (``paper_1901_10084_gb300``) never imports it and shares no code
+with it.
+
+``dykstra.c`` is a plain serial FP64 transcription of Algorithm 1 specialised
+to the metric rows of Eq. (mn1) (Sec. II-B) and walked in the schedules of
+Sec. III-B/C; ``dense.py`` holds brute-force checks built from a dense
+constraint matrix (an LP solve with HiGHS, A^T y, a KKT certificate).
+
+Parity status of each function:
+  * ``sweep`` / ``visit_triplet`` / ``visit_pair``: pinned (halfspace
+    projection property, the worked triangle case of Sec. II-B, the invariant
+    v = v0 - W^{-1} A^T y / eps, monotone dual objective, KKT at convergence,
+    dense LP at small n, the closed-form clustered instance).
+  * ``order`` / ``num_phases``: pinned (brute-force coverage and
+    conflict-freeness, the phase counts and set sizes the paper states).
+  * ``max_violation`` / ``objectives``: pinned by direct definition checks
+    against the dense constraint matrix.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dykstra.c")
+_LIB = os.path.join(_HERE, "_build", "libccoracle.so")
+_lock = threading.Lock()
+_lib = None
+
+SCHEDULES = (0, 1, 2)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, no fast-math)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c99",
+           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        i64, i32, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int32)
+        lib.ora_trank.argtypes = [i64, i64, i64, i64]
+        lib.ora_trank.restype = i64
+        lib.ora_pidx.argtypes = [i64, i64, i64]
+        lib.ora_pidx.restype = i64
+        lib.ora_init.argtypes = [i64, dbl, dp, dp, dp, dp, dp, dp]
+        lib.ora_init.restype = None
+        lib.ora_visit_triplet.argtypes = [i64, dbl, dp, dp, dp, i64, i64, i64, i32]
+        lib.ora_visit_triplet.restype = None
+        lib.ora_visit_pair.argtypes = [i64, dbl, dp, dp, dp, dp, dp, i64, i32]
+        lib.ora_visit_pair.restype = None
+        lib.ora_order.argtypes = [i64, i32, i64, ip, i64]
+        lib.ora_order.restype = i64
+        lib.ora_num_phases.argtypes = [i64, i32, i64]
+        lib.ora_num_phases.restype = i64
+        lib.ora_sweep.argtypes = [i64, i32, i64, dbl, dp, dp, dp, dp, dp, dp, i64]
+        lib.ora_sweep.restype = i64
+        lib.ora_max_violation.argtypes = [i64, dp]
+        lib.ora_max_violation.restype = dbl
+        lib.ora_objectives.argtypes = [i64, dbl, dp, dp, dp, dp, dp, dp]
+        lib.ora_objectives.restype = None
+        _lib = lib
+        return lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def num_pairs(n: int) -> int:
+    return n * (n - 1) // 2
+
+
+def num_triplets(n: int) -> int:
+    return n * (n - 1) * (n - 2) // 6
+
+
+def pidx(n: int, i: int, j: int) -> int:
+    return int(_load().ora_pidx(n, i, j))
+
+
+def trank(n: int, i: int, j: int, k: int) -> int:
+    return int(_load().ora_trank(n, i, j, k))
+
+
+class State:
+    """Oracle state: x, f (packed pairs), y_tri (canonical), y_pair."""
+
+    def __init__(self, n: int, d: np.ndarray, w: np.ndarray, eps: float):
+        self.n = int(n)
+        self.eps = float(eps)
+        P, T = num_pairs(n), num_triplets(n)
+        self.d = np.ascontiguousarray(d, dtype=np.float64)
+        self.w = np.ascontiguousarray(w, dtype=np.float64)
+        assert self.d.shape == (P,) and self.w.shape == (P,)
+        self.winv = np.empty(P)
+        self.x = np.empty(P)
+        self.f = np.empty(P)
+        self.ytri = np.empty(3 * T)
+        self.ypair = np.empty(2 * P)
+        _load().ora_init(n, self.eps, _dp(self.w), _dp(self.winv), _dp(self.x),
+                         _dp(self.f), _dp(self.ytri), _dp(self.ypair))
+
+    def copy(self) -> "State":
+        s = State.__new__(State)
+        s.n, s.eps = self.n, self.eps
+        for k in ("d", "w", "winv", "x", "f", "ytri", "ypair"):
+            setattr(s, k, getattr(self, k).copy())
+        return s
+
+    def sweep(self, schedule: int = 1, tile: int = 16, max_rows: int = -1) -> int:
+        """One pass over all rows in the schedule's order (or its first
+        ``max_rows`` rows).  Returns the number of rows visited."""
+        return int(_load().ora_sweep(self.n, schedule, tile, self.eps, _dp(self.d),
+                                     _dp(self.winv), _dp(self.x), _dp(self.f),
+                                     _dp(self.ytri), _dp(self.ypair), max_rows))
+
+    def visit_triplet(self, i: int, j: int, k: int, rows: int = 3) -> None:
+        _load().ora_visit_triplet(self.n, self.eps, _dp(self.winv), _dp(self.x),
+                                  _dp(self.ytri), i, j, k, rows)
+
+    def visit_pair(self, p: int, rows: int = 2) -> None:
+        _load().ora_visit_pair(self.n, self.eps, _dp(self.d), _dp(self.winv),
+                               _dp(self.x), _dp(self.f), _dp(self.ypair), p, rows)
+
+    def max_violation(self) -> float:
+        return float(_load().ora_max_violation(self.n, _dp(self.x)))
+
+    def objectives(self) -> dict:
+        out = np.zeros(5)
+        _load().ora_objectives(self.n, self.eps, _dp(self.d), _dp(self.w), _dp(self.x),
+                               _dp(self.f), _dp(self.ypair), _dp(out))
+        return {"lp": out[0], "qp_primal": out[1], "dual": out[2],
+                "pair_violation": out[3], "wf": out[4], "gap": out[1] - out[2]}
+
+    def solve(self, tol: float, max_sweeps: int, schedule: int = 1, tile: int = 16,
+              check_every: int = 1) -> int:
+        """Sweep until the largest metric-row violation is <= tol."""
+        for s in range(1, max_sweeps + 1):
+            self.sweep(schedule, tile)
+            if s % check_every == 0 and self.max_violation() <= tol:
+                return s
+        return -1
+
+
+def order(n: int, schedule: int, tile: int = 16) -> np.ndarray:
+    """Visiting order of one sweep: array of (phase, i, j, k) rows."""
+    lib = _load()
+    T = num_triplets(n)
+    rec = np.zeros((max(T, 1), 4), dtype=np.int32)
+    cnt = lib.ora_order(n, schedule, tile,
+                        rec.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), T)
+    assert cnt == T, (cnt, T)
+    return rec[:T]
+
+
+def num_phases(n: int, schedule: int, tile: int = 16) -> int:
+    return int(_load().ora_num_phases(n, schedule, tile))

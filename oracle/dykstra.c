@@ -1,0 +1,334 @@
+/*
+ * Oracle: plain, serial, FP64 Dykstra's method for the regularized
+ * correlation-clustering LP.  TEST INFRASTRUCTURE ONLY: only tests/,
+ * __graft_entry__.smoke() and bench.py's CPU-baseline / reference legs may load
+ * this code.  It shares nothing with the CUDA path.
+ *
+ * Problem (Sec. II-A, Eq. mn1): variables x_ij (distances) and f_ij (slacks)
+ * for every pair i<j; minimize sum_{i<j} w_ij f_ij subject to
+ *     x_ij <= x_ik + x_jk   for every triplet and each choice of the
+ *                           "hypotenuse" pair (three rows per triplet),
+ *     x_ij - d_ij <= f_ij,  d_ij - x_ij <= f_ij   for every pair.
+ * Regularized form (Sec. II-B, Eq. qp): min c^T v + (eps/2) v^T W v, Av <= b,
+ * with v = (x, f), c = (0, w) and W = diag(w, w) (the weights on both blocks).
+ *
+ * Method (Algorithm 1): y := 0, v := -(1/eps) W^{-1} c, then visit the rows
+ * of A cyclically; for row a_i:
+ *     correction  v := v + y_i (1/eps) W^{-1} a_i
+ *     theta       := eps * max(a_i^T v - b_i, 0) / (a_i^T W^{-1} a_i)
+ *     projection  v := v - theta (1/eps) W^{-1} a_i
+ *     dual        y_i := theta.
+ * A metric row has three nonzeros (+1 on the hypotenuse, -1 on the two legs),
+ * so every update touches three entries (Sec. II-B, localized projections).
+ *
+ * Visiting order ("schedules", Sec. III-B): a sweep visits every triplet once
+ * and, for each triplet, its three rows in the order hypotenuse = ij, ik, jk;
+ * after all triplets it visits every pair's two rows (x - f <= d first).
+ *   0: the paper's diagonal listing of the sets S_{i,k} (Fig. "for"): first
+ *      loop x = 1, z = n..3; second loop z = n, x = 2..n-2; inner loop over
+ *      c = 0..floor((z-x-2)/2) with i = x+c, k = z-c; the triplets of one set
+ *      S_{i,k} in ascending middle index j.
+ *   1: triplets grouped by (i+j+k) mod n; phase s = 0..n-1, inside a phase in
+ *      ascending (i, j).  Two triplets of one phase that share two indices
+ *      share the third, so a phase touches every pair at most once (the
+ *      two-triplet lemma of Sec. III-A at triplet granularity).
+ *   2: tiled (the b x b tiling idea of Sec. III-C): indices cut into blocks
+ *      of B; block triples I<=J<=K grouped by (I+J+K) mod Nb (Nb = ceil(n/B)),
+ *      inside a block triple sub-phases t = 0..B-1 over local offsets
+ *      (a, b, c) with (a+b+c) mod B == t, then ascending (a, b).
+ *
+ * Storage: pairs packed row-major, p(i,j) = i*n - i(i+1)/2 + (j-i-1) for
+ * i<j (0-based; the paper is 1-based).  Triangle duals y in canonical order:
+ * lexicographic rank of (i<j<k), times 3, plus the row (0: hyp ij, 1: hyp ik,
+ * 2: hyp jk).  Pair duals: 2 per pair, (x - f <= d, d - x <= f).
+ *
+ * Build with -ffp-contract=off: every product and sum is rounded on its own,
+ * in the order written.
+ */
+#include <stdint.h>
+#include <stddef.h>
+#include <math.h>
+
+static inline int64_t pidx(int64_t n, int64_t i, int64_t j) {
+  return i * n - i * (i + 1) / 2 + (j - i - 1);
+}
+static inline int64_t ch2(int64_t m) { return m < 2 ? 0 : m * (m - 1) / 2; }
+static inline int64_t ch3(int64_t m) { return m < 3 ? 0 : m * (m - 1) * (m - 2) / 6; }
+
+/* lexicographic rank of i<j<k among all triplets of {0..n-1} */
+int64_t ora_trank(int64_t n, int64_t i, int64_t j, int64_t k) {
+  return (ch3(n) - ch3(n - i)) + (ch2(n - 1 - i) - ch2(n - j)) + (k - j - 1);
+}
+
+int64_t ora_pidx(int64_t n, int64_t i, int64_t j) { return pidx(n, i, j); }
+
+/* Algorithm 1's initialisation: y = 0, v = -(1/eps) W^{-1} c with c = (0, w). */
+void ora_init(int64_t n, double eps, const double* w, double* winv, double* x,
+              double* f, double* ytri, double* ypair) {
+  int64_t P = ch2(n), T = ch3(n);
+  for (int64_t p = 0; p < P; ++p) {
+    winv[p] = 1.0 / w[p];                 /* diagonal of W^{-1} (both blocks) */
+    x[p] = 0.0;                           /* c is 0 on the x block */
+    f[p] = -(1.0 / eps) * (w[p] / w[p]);  /* c is w on the f block */
+    ypair[2 * p] = 0.0;
+    ypair[2 * p + 1] = 0.0;
+  }
+  for (int64_t t = 0; t < 3 * T; ++t) ytri[t] = 0.0;
+}
+
+/* One row of Algorithm 1 for the metric constraint x_h - x_a - x_b <= 0
+ * (b_i = 0; a_i = +1 at h, -1 at a and b). */
+static void visit_metric_row(double eps, double* xh, double* xa, double* xb,
+                             double wh, double wa, double wb, double* y) {
+  double corr = *y / eps;                /* y_i (1/eps) */
+  *xh = *xh + corr * wh;                 /* correction: + y_i/eps W^{-1} a_i */
+  *xa = *xa - corr * wa;
+  *xb = *xb - corr * wb;
+  double delta = *xh - *xa - *xb;        /* a_i^T v - b_i */
+  double aWa = wh + wa + wb;             /* a_i^T W^{-1} a_i */
+  double theta = eps * fmax(delta, 0.0) / aWa;
+  double step = theta / eps;             /* theta (1/eps) */
+  *xh = *xh - step * wh;                 /* projection: - theta/eps W^{-1} a_i */
+  *xa = *xa + step * wa;
+  *xb = *xb + step * wb;
+  *y = theta;                            /* dual update */
+}
+
+/* The three metric rows of triplet i<j<k, in the order hyp = ij, ik, jk;
+ * only the first `rows` of them (1..3). */
+static void visit_triplet(int64_t n, double eps, const double* winv, double* x,
+                          double* ytri, int64_t i, int64_t j, int64_t k, int rows) {
+  int64_t pij = pidx(n, i, j), pik = pidx(n, i, k), pjk = pidx(n, j, k);
+  double* y = ytri + 3 * ora_trank(n, i, j, k);
+  visit_metric_row(eps, &x[pij], &x[pik], &x[pjk], winv[pij], winv[pik], winv[pjk], &y[0]);
+  if (rows < 2) return;
+  visit_metric_row(eps, &x[pik], &x[pij], &x[pjk], winv[pik], winv[pij], winv[pjk], &y[1]);
+  if (rows < 3) return;
+  visit_metric_row(eps, &x[pjk], &x[pij], &x[pik], winv[pjk], winv[pij], winv[pik], &y[2]);
+}
+
+void ora_visit_triplet(int64_t n, double eps, const double* winv, double* x,
+                       double* ytri, int64_t i, int64_t j, int64_t k, int rows) {
+  visit_triplet(n, eps, winv, x, ytri, i, j, k, rows);
+}
+
+/* The two rows of pair p: x - f <= d (a = (+1, -1), b = d), then
+ * d - x <= f, i.e. -x - f <= -d (a = (-1, -1), b = -d).  a^T W^{-1} a = 2/w. */
+static void visit_pair(double eps, double d, double wv, double* x, double* f,
+                       double* y, int rows) {
+  double corr = y[0] / eps;
+  *x = *x + corr * wv;
+  *f = *f - corr * wv;
+  double delta = *x - *f - d;
+  double theta = eps * fmax(delta, 0.0) / (wv + wv);
+  double step = theta / eps;
+  *x = *x - step * wv;
+  *f = *f + step * wv;
+  y[0] = theta;
+  if (rows < 2) return;
+  corr = y[1] / eps;
+  *x = *x - corr * wv;
+  *f = *f - corr * wv;
+  delta = -*x - *f + d;
+  theta = eps * fmax(delta, 0.0) / (wv + wv);
+  step = theta / eps;
+  *x = *x + step * wv;
+  *f = *f + step * wv;
+  y[1] = theta;
+}
+
+void ora_visit_pair(int64_t n, double eps, const double* d, const double* winv,
+                    double* x, double* f, double* ypair, int64_t p, int rows) {
+  (void)n;
+  visit_pair(eps, d[p], winv[p], &x[p], &f[p], &ypair[2 * p], rows);
+}
+
+/* ---- walking a schedule ------------------------------------------------ */
+
+typedef struct {
+  int64_t n;
+  double eps;
+  const double* winv;
+  double* x;
+  double* ytri;
+  int64_t rows_left;  /* metric rows still allowed; < 0: no limit */
+  int32_t* rec;       /* when non-NULL: record (phase, i, j, k) instead */
+  int64_t rec_cap;
+  int64_t count;      /* triplets reached so far */
+  int64_t phase;
+} walk_t;
+
+/* returns 0 when the walk must stop */
+static int walk_step(walk_t* w, int64_t i, int64_t j, int64_t k) {
+  if (w->rec) {
+    if (w->count < w->rec_cap) {
+      int32_t* r = w->rec + 4 * w->count;
+      r[0] = (int32_t)w->phase; r[1] = (int32_t)i; r[2] = (int32_t)j; r[3] = (int32_t)k;
+    }
+    w->count++;
+    return 1;
+  }
+  int rows = 3;
+  if (w->rows_left >= 0) {
+    if (w->rows_left == 0) return 0;
+    if (w->rows_left < 3) rows = (int)w->rows_left;
+    w->rows_left -= rows;
+  }
+  visit_triplet(w->n, w->eps, w->winv, w->x, w->ytri, i, j, k, rows);
+  w->count++;
+  return 1;
+}
+
+/* Schedule 0: the listing of Fig. "for" with 1-based x, z, c, i, k as printed. */
+static int walk_sched0(walk_t* w) {
+  int64_t n = w->n;
+  int64_t x = 1, z, c, g, i, k, j;
+  for (z = n; z >= 3; --z) {                 /* first double loop */
+    g = (z - x - 2) / 2;
+    for (c = 0; c <= g; ++c) {
+      i = x + c;
+      k = z - c;
+      for (j = i + 1; j <= k - 1; ++j)       /* the set S_{i,k} */
+        if (!walk_step(w, i - 1, j - 1, k - 1)) return 0;
+    }
+    w->phase++;
+  }
+  z = n;
+  for (x = 2; x <= n - 2; ++x) {             /* second double loop */
+    g = (z - x - 2) / 2;
+    for (c = 0; c <= g; ++c) {
+      i = x + c;
+      k = z - c;
+      for (j = i + 1; j <= k - 1; ++j)
+        if (!walk_step(w, i - 1, j - 1, k - 1)) return 0;
+    }
+    w->phase++;
+  }
+  return 1;
+}
+
+/* Schedule 1: phase s holds the triplets with (i+j+k) mod n == s. */
+static int walk_sched1(walk_t* w) {
+  int64_t n = w->n;
+  for (int64_t s = 0; s < n; ++s) {
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = i + 1; j < n; ++j) {
+        int64_t k = ((s - i - j) % n + n) % n;   /* the one k of this phase */
+        if (k > j)
+          if (!walk_step(w, i, j, k)) return 0;
+      }
+    w->phase++;
+  }
+  return 1;
+}
+
+/* Schedule 2: tiled, block size B. */
+static int walk_sched2(walk_t* w, int64_t B) {
+  int64_t n = w->n;
+  int64_t nb = (n + B - 1) / B;
+  for (int64_t g = 0; g < nb; ++g) {
+    for (int64_t I = 0; I < nb; ++I)
+      for (int64_t J = I; J < nb; ++J)
+        for (int64_t K = J; K < nb; ++K) {
+          if ((I + J + K) % nb != g) continue;
+          for (int64_t t = 0; t < B; ++t)
+            for (int64_t a = 0; a < B; ++a)
+              for (int64_t b = 0; b < B; ++b) {
+                int64_t c = ((t - a - b) % B + B) % B;
+                int64_t i = I * B + a, j = J * B + b, k = K * B + c;
+                if (i < j && j < k && k < n)
+                  if (!walk_step(w, i, j, k)) return 0;
+              }
+        }
+    w->phase++;
+  }
+  return 1;
+}
+
+static int walk_schedule(walk_t* w, int sched, int64_t B) {
+  if (sched == 0) return walk_sched0(w);
+  if (sched == 1) return walk_sched1(w);
+  return walk_sched2(w, B);
+}
+
+/* Record the visiting order: rec[4*t .. 4*t+3] = (phase, i, j, k) for the
+ * t-th triplet visited.  Returns the number of triplets in one sweep. */
+int64_t ora_order(int64_t n, int sched, int64_t B, int32_t* rec, int64_t cap) {
+  walk_t w = {n, 0.0, NULL, NULL, NULL, -1, rec, cap, 0, 0};
+  walk_schedule(&w, sched, B);
+  return w.count;
+}
+
+/* Number of phases of a schedule. */
+int64_t ora_num_phases(int64_t n, int sched, int64_t B) {
+  int32_t dummy[4];
+  walk_t w = {n, 0.0, NULL, NULL, NULL, -1, dummy, 0, 0, 0};
+  walk_schedule(&w, sched, B);
+  return w.phase;
+}
+
+/* One sweep: every triplet in schedule order, then every pair.  With
+ * max_rows >= 0 the sweep stops after that many rows (metric rows first, then
+ * pair rows), for step-by-step checks.  Returns the rows visited. */
+int64_t ora_sweep(int64_t n, int sched, int64_t B, double eps, const double* d,
+                  const double* winv, double* x, double* f, double* ytri,
+                  double* ypair, int64_t max_rows) {
+  walk_t w = {n, eps, winv, x, ytri, max_rows, NULL, 0, 0, 0};
+  int64_t rows = 0;
+  if (!walk_schedule(&w, sched, B)) return max_rows;
+  rows = max_rows >= 0 ? max_rows - w.rows_left : 3 * w.count;
+  int64_t P = ch2(n);
+  for (int64_t p = 0; p < P; ++p) {
+    int r = 2;
+    if (max_rows >= 0) {
+      int64_t left = max_rows - rows;
+      if (left <= 0) break;
+      if (left < 2) r = (int)left;
+    }
+    visit_pair(eps, d[p], winv[p], &x[p], &f[p], &ypair[2 * p], r);
+    rows += r;
+  }
+  return rows;
+}
+
+/* Largest violation of a metric row on the current x: max over triplets and
+ * hypotenuse choices of max(0, x_h - x_a - x_b). */
+double ora_max_violation(int64_t n, const double* x) {
+  double m = 0.0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = i + 1; j < n; ++j)
+      for (int64_t k = j + 1; k < n; ++k) {
+        double xij = x[pidx(n, i, j)], xik = x[pidx(n, i, k)], xjk = x[pidx(n, j, k)];
+        double v0 = xij - xik - xjk, v1 = xik - xij - xjk, v2 = xjk - xij - xik;
+        if (v0 > m) m = v0;
+        if (v1 > m) m = v1;
+        if (v2 > m) m = v2;
+      }
+  return m;
+}
+
+/* out[0] = LP objective sum w|x - d|   (Eq. mn1 at f = |x - d|)
+ * out[1] = QP primal  sum w f + (eps/2) sum w (x^2 + f^2)   (Eq. qp)
+ * out[2] = dual objective -b^T y - (eps/2) v^T W v with b^T y = sum d (y+ - y-)
+ * out[3] = largest pair-row violation max(0, x - f - d, d - x - f)
+ * out[4] = sum w f (the LP objective at the current slacks) */
+void ora_objectives(int64_t n, double eps, const double* d, const double* w,
+                    const double* x, const double* f, const double* ypair,
+                    double* out) {
+  int64_t P = ch2(n);
+  double lp = 0.0, wf = 0.0, quad = 0.0, by = 0.0, pv = 0.0;
+  for (int64_t p = 0; p < P; ++p) {
+    lp += w[p] * fabs(x[p] - d[p]);
+    wf += w[p] * f[p];
+    quad += w[p] * (x[p] * x[p] + f[p] * f[p]);
+    by += d[p] * (ypair[2 * p] - ypair[2 * p + 1]);
+    double v0 = x[p] - f[p] - d[p], v1 = d[p] - x[p] - f[p];
+    if (v0 > pv) pv = v0;
+    if (v1 > pv) pv = v1;
+  }
+  out[0] = lp;
+  out[1] = wf + 0.5 * eps * quad;
+  out[2] = -by - 0.5 * eps * quad;
+  out[3] = pv;
+  out[4] = wf;
+}
