@@ -1,0 +1,165 @@
+/*
+ * ccdyk: Dykstra's projection method for the metric-constrained LP relaxation
+ * of correlation clustering, run on one GPU under conflict-free parallel
+ * schedules.  Plain C ABI: host or device pointers and sizes only.
+ *
+ * The problem (Sec. II-A, Eq. mn1): for n objects, dissimilarities d_ij and
+ * weights w_ij > 0 on the P = n(n-1)/2 pairs i<j, find distances x_ij and
+ * slacks f_ij minimizing sum w_ij f_ij subject to x_ij <= x_ik + x_jk for all
+ * triplets and hypotenuse choices, x_ij - d_ij <= f_ij and d_ij - x_ij <= f_ij.
+ * It is solved in the regularized form of Eq. (qp),
+ *     min c^T v + (eps/2) v^T W v  s.t.  A v <= b,   v = (x, f), c = (0, w),
+ *     W = diag(w, w),
+ * by Dykstra's method (Algorithm 1), which keeps one dual y_r >= 0 per row of
+ * A.  One "sweep" visits every row once: the three metric rows of every
+ * triplet (hypotenuse ij, then ik, then jk), phase by phase in the chosen
+ * schedule (Sec. III-B/C), then the two rows of every pair.
+ *
+ * Layouts of host arrays exchanged through this ABI:
+ *   pairs     P = n(n-1)/2 doubles, packed row-major over i<j (0-based):
+ *             p(i,j) = i*n - i(i+1)/2 + (j-i-1).
+ *   y_tri     3 doubles per triplet, triplets in lexicographic order of
+ *             (i<j<k), rows in the order hypotenuse ij, ik, jk.
+ *   y_pair    2 doubles per pair in packed order: row x - f <= d, then
+ *             row d - x <= f.
+ * The duals returned are the y of Algorithm 1 (Lagrange multipliers of
+ * Eq. qp), whatever scaling the device store uses.
+ *
+ * Errors: every int-returning call returns CC_OK (0) or one of the CC_ERR_*
+ * codes; cc_last_error() then holds a message.  No call aborts the process
+ * and no exception crosses the ABI.  A handle is not thread-safe: calls on
+ * one handle must not overlap.
+ */
+#ifndef CCDYK_H
+#define CCDYK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CC_OK 0
+#define CC_ERR_ARG 1           /* null pointer, n < 3, w <= 0, non-finite input, eps <= 0, bad option */
+#define CC_ERR_OOM 2           /* device or host allocation failed */
+#define CC_ERR_CUDA 3          /* a CUDA call failed (message holds the CUDA error) */
+#define CC_ERR_TIMEOUT 4       /* a grid barrier inside a sweep hit its time limit */
+#define CC_ERR_NOT_CONVERGED 5 /* cc_solve reached max_sweeps */
+#define CC_ERR_UNSUPPORTED 6   /* valid request this build does not serve */
+
+/* Visiting orders (Sec. III-B/C).  Every schedule visits each triplet once
+ * per sweep; triplets of one phase touch pairwise-disjoint pairs, so a phase
+ * runs in parallel with the same result as any serial order of it. */
+#define CC_SCHED_DIAGONAL 0 /* the paper's listing: phases are the diagonals
+                               i+k = const of the (i,k) grid; a set S_{i,k}
+                               is one serial chain over ascending j */
+#define CC_SCHED_SUMMOD 1   /* phase s: triplets with (i+j+k) mod n = s */
+#define CC_SCHED_TILED 2    /* B x B tiles: block triples I<=J<=K with
+                               (I+J+K) mod ceil(n/B) = g; inside a block triple
+                               sub-phases (a+b+c) mod B = t on local offsets */
+
+#define CC_PREC_FP64 0        /* x, f and duals in FP64 */
+#define CC_PREC_FP32_REFINE 1 /* bulk sweeps in FP32, final sweeps in FP64 */
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc
+ * returns a device pointer of at least `bytes` bytes valid on `stream`, or
+ * NULL; free releases it. */
+typedef void* (*cc_alloc_fn)(void* ctx, size_t bytes, void* stream);
+typedef void (*cc_free_fn)(void* ctx, void* ptr, void* stream);
+
+typedef struct cc_opts {
+  double eps;               /* regularization eps of Eq. (qp), > 0; default 0.2 */
+  int32_t schedule;         /* CC_SCHED_*; default CC_SCHED_TILED */
+  int32_t tile;             /* B for the tiled schedule and the x layout: 8, 16 or 32; default 16 */
+  int32_t precision;        /* CC_PREC_*; default CC_PREC_FP64 */
+  int32_t exact;            /* 1: each row computed operation by operation as
+                               Algorithm 1 states it (FP64 only; bit-identical
+                               to a serial IEEE double evaluation in the same
+                               visiting order); 0: fused form (default) */
+  int32_t check_every;      /* cc_solve: sweeps between convergence checks; default 10 */
+  int32_t device;           /* CUDA device ordinal; default 0 */
+  double barrier_timeout_s; /* limit on one grid-barrier wait; default 2.0 */
+  void* stream;             /* cudaStream_t for all work; NULL = legacy default stream */
+  cc_alloc_fn alloc;        /* NULL: cudaMalloc / cudaFree */
+  cc_free_fn free;
+  void* alloc_ctx;
+  int32_t grid;             /* CTAs of a sweep launch; 0 = as many as fit */
+  int32_t debug_skip_cta;   /* test hook: this CTA skips its first barrier
+                               arrival (-1 = off); the sweep then ends with
+                               CC_ERR_TIMEOUT */
+} cc_opts;
+
+typedef struct cc_stats {
+  int64_t sweeps;          /* sweeps run since cc_create (or cc_set_state) */
+  double max_violation;    /* max over triplets and rows of max(0, x_h - x_a - x_b) */
+  double pair_violation;   /* max over pairs of max(0, x - f - d, d - x - f) */
+  double lp_objective;     /* sum w |x - d|: objective of Eq. (mn1) at f = |x - d| */
+  double wf;               /* sum w f at the current slacks */
+  double qp_primal;        /* c^T v + (eps/2) v^T W v */
+  double dual_objective;   /* -b^T y - (eps/2) v^T W v (valid while v = v0 - W^-1 A^T y / eps) */
+  double gap;              /* qp_primal - dual_objective */
+  double last_sweep_ms;    /* device time of the most recent sweep launch */
+} cc_stats;
+
+typedef struct cc_handle cc_handle;
+
+/* Fill *opts with the defaults listed above. */
+void cc_opts_default(cc_opts* opts);
+
+/* Create a solver for n objects.  d, w: host arrays of P doubles (packed
+ * order); they are copied, the caller keeps ownership.  opts may be NULL.
+ * Sets x = 0, f = -1/eps, all duals 0 (Algorithm 1's initialisation with
+ * c = (0, w), W = diag(w, w)).  On error *out is NULL. */
+int cc_create(cc_handle** out, int64_t n, const double* d, const double* w, const cc_opts* opts);
+
+/* Same, with d and w already on the device (P doubles each, packed order,
+ * caller-owned, read during this call only). */
+int cc_create_device(cc_handle** out, int64_t n, const double* d_dev, const double* w_dev,
+                     const cc_opts* opts);
+
+/* Run k >= 0 full sweeps, asynchronously on the handle's stream.  A barrier
+ * time-out inside a sweep is reported by the next synchronizing call. */
+int cc_sweep(cc_handle* h, int64_t k);
+
+/* Convergence quantities at the current state (synchronizes). */
+int cc_check(cc_handle* h, cc_stats* st);
+
+/* Sweep until max_violation <= tol (checked every check_every sweeps) or
+ * max_sweeps sweeps have run; *sweeps_done (nullable) gets the count.
+ * Returns CC_ERR_NOT_CONVERGED when the cap is reached. */
+int cc_solve(cc_handle* h, double tol, int64_t max_sweeps, int64_t* sweeps_done);
+
+/* Copy x and f (each P doubles, packed order, caller-owned host buffers;
+ * f may be NULL).  Synchronizes. */
+int cc_get_x(cc_handle* h, double* x, double* f);
+
+/* Copy the duals y of triplets [tri_first, tri_first + tri_count) (3 doubles
+ * each, canonical order) into y_tri, and of all pairs (2P doubles) into
+ * y_pair.  Either buffer may be NULL.  Host buffers, caller-owned. */
+int cc_get_duals(cc_handle* h, double* y_tri, double* y_pair, int64_t tri_first, int64_t tri_count);
+
+/* Overwrite the state (x, f: P doubles; y_tri: 3 C(n,3) doubles; y_pair:
+ * 2P doubles; host, canonical order) and reset the sweep count.  Used for
+ * checkpoint/resume and warm starts. */
+int cc_set_state(cc_handle* h, const double* x, const double* f, const double* y_tri,
+                 const double* y_pair);
+
+/* Counters of the last check plus sweeps and last sweep time (no device work). */
+int cc_get_stats(cc_handle* h, cc_stats* st);
+
+/* Device bytes held by the handle. */
+int64_t cc_device_bytes(const cc_handle* h);
+
+/* Release everything the handle owns.  NULL is a no-op. */
+void cc_destroy(cc_handle* h);
+
+/* Message of the last failed call on h (or of the last failed cc_create when
+ * h is NULL).  Never NULL. */
+const char* cc_last_error(const cc_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCDYK_H */

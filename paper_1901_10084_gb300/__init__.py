@@ -1,0 +1,163 @@
+"""GPU Dykstra solver for the metric-constrained LP relaxation of correlation
+clustering (parallel projection method with conflict-free schedules).
+
+The solver itself is the CUDA library ``libccdyk.so`` behind the C ABI of
+``include/ccdyk.h``; ``_native`` mirrors that ABI name for name and ``Solver``
+wraps it with PyTorch's stream and caching allocator.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native
+from ._native import (CCError, CC_OK, CC_ERR_ARG, CC_ERR_OOM, CC_ERR_CUDA, CC_ERR_TIMEOUT,
+                      CC_ERR_NOT_CONVERGED, CC_ERR_UNSUPPORTED, CC_SCHED_DIAGONAL,
+                      CC_SCHED_SUMMOD, CC_SCHED_TILED, CC_PREC_FP64, CC_PREC_FP32_REFINE,
+                      cc_opts_default, cc_create, cc_create_device, cc_sweep, cc_check, cc_solve,
+                      cc_get_x, cc_get_duals, cc_set_state, cc_get_stats, cc_device_bytes,
+                      cc_destroy, cc_last_error)
+from .buildlib import build
+
+__all__ = [
+    "Solver", "CCError", "build", "num_pairs", "num_triplets",
+    "cc_opts_default", "cc_create", "cc_create_device", "cc_sweep", "cc_check", "cc_solve",
+    "cc_get_x", "cc_get_duals", "cc_set_state", "cc_get_stats", "cc_device_bytes",
+    "cc_destroy", "cc_last_error",
+]
+
+SCHEDULES = {"diagonal": CC_SCHED_DIAGONAL, "summod": CC_SCHED_SUMMOD, "tiled": CC_SCHED_TILED}
+PRECISIONS = {"fp64": CC_PREC_FP64, "fp32_refine": CC_PREC_FP32_REFINE}
+
+
+def num_pairs(n: int) -> int:
+    return n * (n - 1) // 2
+
+
+def num_triplets(n: int) -> int:
+    return n * (n - 1) * (n - 2) // 6
+
+
+class _TorchAllocator:
+    """Routes the library's device allocations through PyTorch's caching
+    allocator (the callbacks stay alive as long as the solver)."""
+
+    def __init__(self, device: int):
+        import torch
+        self._torch = torch
+        self.device = device
+
+        def _alloc(ctx, nbytes, stream):
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, int(stream or 0)))
+
+        def _free(ctx, ptr, stream):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc = _native.ALLOC_FN(_alloc)
+        self.free = _native.FREE_FN(_free)
+
+
+class Solver:
+    """One correlation-clustering LP instance on one GPU.
+
+    ``d`` and ``w`` are the packed pair arrays (P = n(n-1)/2 doubles, row-major
+    over i<j).  ``stream`` is a ``torch.cuda.Stream`` (default: the current
+    stream); with ``torch_alloc`` the device memory comes from PyTorch's
+    caching allocator.
+    """
+
+    def __init__(self, n, d, w, eps=0.2, schedule="tiled", tile=16, precision="fp64",
+                 exact=False, check_every=10, device=0, stream=None, torch_alloc=True,
+                 barrier_timeout_s=2.0, grid=0, debug_skip_cta=-1, on_device=False):
+        o = cc_opts_default()
+        o.eps = float(eps)
+        o.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
+        o.tile = int(tile)
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.exact = 1 if exact else 0
+        o.check_every = int(check_every)
+        o.device = int(device)
+        o.barrier_timeout_s = float(barrier_timeout_s)
+        o.grid = int(grid)
+        o.debug_skip_cta = int(debug_skip_cta)
+        self._alloc = None
+        try:
+            import torch
+            if stream is None:
+                stream = torch.cuda.current_stream(device)
+            o.stream = ctypes.c_void_p(int(stream.cuda_stream))
+            self.stream = stream
+            if torch_alloc:
+                self._alloc = _TorchAllocator(device)
+                o.alloc = self._alloc.alloc
+                o.free = self._alloc.free
+        except ImportError:
+            self.stream = None
+        self.n = int(n)
+        self.eps = float(eps)
+        self.opts = o
+        if on_device:
+            self.h = cc_create_device(self.n, int(d.data_ptr()), int(w.data_ptr()), o)
+        else:
+            d = np.ascontiguousarray(d, dtype=np.float64)
+            w = np.ascontiguousarray(w, dtype=np.float64)
+            P = num_pairs(self.n)
+            if d.shape != (P,) or w.shape != (P,):
+                raise ValueError(f"d and w must have {P} entries")
+            self.h = cc_create(self.n, d, w, o)
+
+    # ---- thin forwards
+    def sweep(self, k: int = 1) -> None:
+        cc_sweep(self.h, k)
+
+    def check(self) -> dict:
+        return cc_check(self.h).as_dict()
+
+    def solve(self, tol: float, max_sweeps: int) -> tuple[bool, int]:
+        """Sweep until the largest metric-row violation is <= tol; returns
+        (converged, sweeps run)."""
+        rc, done = cc_solve(self.h, tol, max_sweeps)
+        return rc == CC_OK, done
+
+    def get_x(self):
+        P = num_pairs(self.n)
+        x, f = np.empty(P), np.empty(P)
+        cc_get_x(self.h, x, f)
+        return x, f
+
+    def get_duals(self, first: int = 0, count: int | None = None, pairs: bool = True):
+        T = num_triplets(self.n)
+        if count is None:
+            count = T - first
+        yt = np.empty(3 * count)
+        yp = np.empty(2 * num_pairs(self.n)) if pairs else None
+        cc_get_duals(self.h, yt, yp, first, count)
+        return yt, yp
+
+    def set_state(self, x, f, y_tri, y_pair) -> None:
+        c = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+        cc_set_state(self.h, c(x), c(f), c(y_tri), c(y_pair))
+
+    def stats(self) -> dict:
+        return cc_get_stats(self.h).as_dict()
+
+    def device_bytes(self) -> int:
+        return cc_device_bytes(self.h)
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None:
+            cc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,216 @@
+"""ctypes binding of the C ABI in include/ccdyk.h (argument marshalling only).
+
+Every function here forwards to libccdyk.so under the same name; all solver
+work runs in that library's CUDA kernels.  Loading fails loudly when the
+library has not been built: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import buildlib as _build
+
+CC_OK = 0
+CC_ERR_ARG = 1
+CC_ERR_OOM = 2
+CC_ERR_CUDA = 3
+CC_ERR_TIMEOUT = 4
+CC_ERR_NOT_CONVERGED = 5
+CC_ERR_UNSUPPORTED = 6
+
+CC_SCHED_DIAGONAL = 0
+CC_SCHED_SUMMOD = 1
+CC_SCHED_TILED = 2
+
+CC_PREC_FP64 = 0
+CC_PREC_FP32_REFINE = 1
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class cc_opts(ctypes.Structure):
+    _fields_ = [
+        ("eps", ctypes.c_double),
+        ("schedule", ctypes.c_int32),
+        ("tile", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("exact", ctypes.c_int32),
+        ("check_every", ctypes.c_int32),
+        ("device", ctypes.c_int32),
+        ("barrier_timeout_s", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+        ("alloc", ALLOC_FN),
+        ("free", FREE_FN),
+        ("alloc_ctx", ctypes.c_void_p),
+        ("grid", ctypes.c_int32),
+        ("debug_skip_cta", ctypes.c_int32),
+    ]
+
+
+class cc_stats(ctypes.Structure):
+    _fields_ = [
+        ("sweeps", ctypes.c_int64),
+        ("max_violation", ctypes.c_double),
+        ("pair_violation", ctypes.c_double),
+        ("lp_objective", ctypes.c_double),
+        ("wf", ctypes.c_double),
+        ("qp_primal", ctypes.c_double),
+        ("dual_objective", ctypes.c_double),
+        ("gap", ctypes.c_double),
+        ("last_sweep_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ("cc_opts_default", "cc_create", "cc_create_device", "cc_sweep", "cc_check",
+           "cc_solve", "cc_get_x", "cc_get_duals", "cc_set_state", "cc_get_stats",
+           "cc_device_bytes", "cc_destroy", "cc_last_error")
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libccdyk.so; raise if it is missing (no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(
+                f"libccdyk.so not built at {_build.LIB}; run __graft_entry__.build() "
+                "(the CUDA library is the only implementation)")
+        lib = ctypes.CDLL(_build.LIB)
+        H = ctypes.c_void_p
+        HP = ctypes.POINTER(ctypes.c_void_p)
+        i64, dp = ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+        lib.cc_opts_default.argtypes = [ctypes.POINTER(cc_opts)]
+        lib.cc_opts_default.restype = None
+        lib.cc_create.argtypes = [HP, i64, dp, dp, ctypes.POINTER(cc_opts)]
+        lib.cc_create.restype = ctypes.c_int
+        lib.cc_create_device.argtypes = [HP, i64, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(cc_opts)]
+        lib.cc_create_device.restype = ctypes.c_int
+        lib.cc_sweep.argtypes = [H, i64]
+        lib.cc_sweep.restype = ctypes.c_int
+        lib.cc_check.argtypes = [H, ctypes.POINTER(cc_stats)]
+        lib.cc_check.restype = ctypes.c_int
+        lib.cc_solve.argtypes = [H, ctypes.c_double, i64, ctypes.POINTER(ctypes.c_int64)]
+        lib.cc_solve.restype = ctypes.c_int
+        lib.cc_get_x.argtypes = [H, dp, dp]
+        lib.cc_get_x.restype = ctypes.c_int
+        lib.cc_get_duals.argtypes = [H, dp, dp, i64, i64]
+        lib.cc_get_duals.restype = ctypes.c_int
+        lib.cc_set_state.argtypes = [H, dp, dp, dp, dp]
+        lib.cc_set_state.restype = ctypes.c_int
+        lib.cc_get_stats.argtypes = [H, ctypes.POINTER(cc_stats)]
+        lib.cc_get_stats.restype = ctypes.c_int
+        lib.cc_device_bytes.argtypes = [H]
+        lib.cc_device_bytes.restype = i64
+        lib.cc_destroy.argtypes = [H]
+        lib.cc_destroy.restype = None
+        lib.cc_last_error.argtypes = [H]
+        lib.cc_last_error.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+class CCError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def _dp(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(rc: int, h) -> None:
+    if rc != CC_OK:
+        msg = load().cc_last_error(h)
+        raise CCError(rc, msg.decode() if msg else "")
+
+
+# ---- same names as the C ABI ---------------------------------------------
+
+def cc_opts_default() -> cc_opts:
+    o = cc_opts()
+    load().cc_opts_default(ctypes.byref(o))
+    return o
+
+
+def cc_create(n: int, d, w, opts: cc_opts | None = None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    rc = load().cc_create(ctypes.byref(h), n, _dp(d), _dp(w), ctypes.byref(opts) if opts else None)
+    _check(rc, None)
+    return h
+
+
+def cc_create_device(n: int, d_ptr: int, w_ptr: int, opts: cc_opts | None = None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    rc = load().cc_create_device(ctypes.byref(h), n, ctypes.c_void_p(d_ptr), ctypes.c_void_p(w_ptr),
+                                 ctypes.byref(opts) if opts else None)
+    _check(rc, None)
+    return h
+
+
+def cc_sweep(h, k: int) -> None:
+    _check(load().cc_sweep(h, k), h)
+
+
+def cc_check(h) -> cc_stats:
+    st = cc_stats()
+    _check(load().cc_check(h, ctypes.byref(st)), h)
+    return st
+
+
+def cc_solve(h, tol: float, max_sweeps: int) -> tuple[int, int]:
+    """Returns (status, sweeps_done); status is CC_OK or CC_ERR_NOT_CONVERGED."""
+    done = ctypes.c_int64(0)
+    rc = load().cc_solve(h, tol, max_sweeps, ctypes.byref(done))
+    if rc not in (CC_OK, CC_ERR_NOT_CONVERGED):
+        _check(rc, h)
+    return rc, done.value
+
+
+def cc_get_x(h, x, f=None) -> None:
+    _check(load().cc_get_x(h, _dp(x), _dp(f)), h)
+
+
+def cc_get_duals(h, y_tri, y_pair, tri_first: int = 0, tri_count: int = 0) -> None:
+    _check(load().cc_get_duals(h, _dp(y_tri), _dp(y_pair), tri_first, tri_count), h)
+
+
+def cc_set_state(h, x, f, y_tri, y_pair) -> None:
+    _check(load().cc_set_state(h, _dp(x), _dp(f), _dp(y_tri), _dp(y_pair)), h)
+
+
+def cc_get_stats(h) -> cc_stats:
+    st = cc_stats()
+    _check(load().cc_get_stats(h, ctypes.byref(st)), h)
+    return st
+
+
+def cc_device_bytes(h) -> int:
+    return int(load().cc_device_bytes(h))
+
+
+def cc_destroy(h) -> None:
+    load().cc_destroy(h)
+
+
+def cc_last_error(h=None) -> str:
+    m = load().cc_last_error(h)
+    return m.decode() if m else ""

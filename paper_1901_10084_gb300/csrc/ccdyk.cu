@@ -1,0 +1,657 @@
+// C ABI of the GPU Dykstra solver (declared in include/ccdyk.h): handle
+// state, device memory, schedule tables and kernel launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ccdyk.h"
+#include "common.cuh"
+#include "tiled.cuh"
+
+using namespace ccd;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Alloc {
+  void* p;
+  size_t bytes;
+};
+
+}  // namespace
+
+struct cc_handle {
+  int64_t n = 0, P = 0, T3 = 0;
+  int B = 16, nb = 0, ntiles = 0, nbt = 0, max_bt_phase = 0;
+  cc_opts o{};
+  cudaStream_t st = nullptr;
+  int dev = 0, sms = 0;
+  bool unitw = true;
+  bool fp32 = false;   // state currently held in FP32 (bulk phase of CC_PREC_FP32_REFINE)
+  size_t esz = 8;      // element size of the state
+  // device state (element type double, or float while fp32)
+  void* x = nullptr;
+  void* f = nullptr;
+  void* d = nullptr;
+  void* winv = nullptr;
+  void* zt = nullptr;
+  void* zp = nullptr;
+  int64_t tile_elems = 0;   // ntiles * B * B
+  int64_t zt_elems = 0;     // nbt * 3 * B^3
+  // schedule tables
+  int* bt_list = nullptr;
+  int* bt_off = nullptr;
+  int* tile_list = nullptr;
+  int* bt_rank = nullptr;
+  // scratch
+  Ctl* ctl = nullptr;
+  double* part = nullptr;    // reduction partials
+  int part_cap = 0;
+  double* stage = nullptr;   // layout staging
+  int64_t stage_elems = 0;
+  double* h_pin = nullptr;   // pinned host mirror of small results
+  // launch config
+  int sweep_grid = 0, sweep_threads = 0;
+  // bookkeeping
+  int64_t sweeps = 0;
+  cc_stats last{};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool ev_recorded = false;
+  std::vector<Alloc> allocs;
+  int64_t dev_bytes = 0;
+  std::string err;
+};
+
+namespace {
+
+int fail(cc_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg; else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(cc_handle* h, cudaError_t e, const char* what) {
+  return fail(h, CC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                   \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+void* dalloc(cc_handle* h, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (h->o.alloc) {
+    p = h->o.alloc(h->o.alloc_ctx, bytes, h->st);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) {
+    h->allocs.push_back({p, bytes});
+    h->dev_bytes += (int64_t)bytes;
+  }
+  return p;
+}
+
+void dfree(cc_handle* h, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < h->allocs.size(); ++i) {
+    if (h->allocs[i].p == p) {
+      h->dev_bytes -= (int64_t)h->allocs[i].bytes;
+      h->allocs.erase(h->allocs.begin() + (long)i);
+      break;
+    }
+  }
+  if (h->o.free) h->o.free(h->o.alloc_ctx, p, h->st);
+  else cudaFree(p);
+}
+
+int grid_for(cc_handle* h, int64_t work, int threads) {
+  int64_t g = (work + threads - 1) / threads;
+  g = std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)h->sms * 8));
+  return (int)g;
+}
+
+// ------------------------------------------------------------ dispatch
+
+template <typename T, bool EXACT, bool UNITW, int B>
+void* sweep_kernel_ptr() {
+  return (void*)k_sweep_tiled<T, EXACT, UNITW, B>;
+}
+
+template <typename T, bool EXACT, bool UNITW>
+void* sweep_kernel_b(int B) {
+  switch (B) {
+    case 8: return sweep_kernel_ptr<T, EXACT, UNITW, 8>();
+    case 16: return sweep_kernel_ptr<T, EXACT, UNITW, 16>();
+    default: return sweep_kernel_ptr<T, EXACT, UNITW, 32>();
+  }
+}
+
+void* sweep_kernel(cc_handle* h) {
+  const bool ex = h->o.exact != 0;
+  if (h->fp32) return h->unitw ? sweep_kernel_b<float, false, true>(h->B) : sweep_kernel_b<float, false, false>(h->B);
+  if (ex) return h->unitw ? sweep_kernel_b<double, true, true>(h->B) : sweep_kernel_b<double, true, false>(h->B);
+  return h->unitw ? sweep_kernel_b<double, false, true>(h->B) : sweep_kernel_b<double, false, false>(h->B);
+}
+
+int threads_for_tile(int B) { return B * B < 256 ? B * B : 256; }
+
+template <typename T>
+TiledArgs<T> tiled_args(cc_handle* h) {
+  TiledArgs<T> a;
+  a.n = (int)h->n;
+  a.nb = h->nb;
+  a.ntiles = h->ntiles;
+  a.x = (T*)h->x;
+  a.f = (T*)h->f;
+  a.d = (const T*)h->d;
+  a.winv = (const T*)h->winv;
+  a.zt = (T*)h->zt;
+  a.zp = (T*)h->zp;
+  a.bt_list = h->bt_list;
+  a.bt_off = h->bt_off;
+  a.tile_list = h->tile_list;
+  a.ctl = h->ctl;
+  a.timeout_ns = (long long)(h->o.barrier_timeout_s * 1e9);
+  a.eps = (T)h->o.eps;
+  a.r_unit = (T)(1.0 / 3.0);
+  a.skip_cta = h->o.debug_skip_cta;
+  return a;
+}
+
+int configure_sweep(cc_handle* h) {
+  void* k = sweep_kernel(h);
+  const int threads = threads_for_tile(h->B);
+  int per_sm = 0;
+  CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0));
+  if (per_sm < 1) return fail(h, CC_ERR_CUDA, "sweep kernel does not fit on an SM");
+  int cap = per_sm * h->sms;
+  int g = h->o.grid > 0 ? std::min(h->o.grid, cap) : std::min(cap, std::max(1, h->max_bt_phase));
+  h->sweep_grid = g;
+  h->sweep_threads = threads;
+  return CC_OK;
+}
+
+int launch_sweep(cc_handle* h) {
+  void* k = sweep_kernel(h);
+  CK(h, cudaMemsetAsync(&h->ctl->arrive, 0, sizeof(unsigned), h->st));
+  if (h->fp32) {
+    TiledArgs<float> a = tiled_args<float>(h);
+    void* args[] = {&a};
+    CK(h, cudaLaunchCooperativeKernel(k, h->sweep_grid, h->sweep_threads, args, 0, h->st));
+  } else {
+    TiledArgs<double> a = tiled_args<double>(h);
+    void* args[] = {&a};
+    CK(h, cudaLaunchCooperativeKernel(k, h->sweep_grid, h->sweep_threads, args, 0, h->st));
+  }
+  return CC_OK;
+}
+
+// ------------------------------------------------------------ tables
+
+int build_tables(cc_handle* h) {
+  const int nb = h->nb, B = h->B;
+  std::vector<int> list, off(nb + 1, 0), rank((size_t)nb * nb * nb, -1), tiles;
+  for (int g = 0; g < nb; ++g) {
+    off[g] = (int)list.size();
+    for (int I = 0; I < nb; ++I)
+      for (int J = I; J < nb; ++J) {
+        int K = ((g - I - J) % nb + 2 * nb) % nb;
+        if (K < J) continue;
+        rank[((size_t)I * nb + J) * nb + K] = (int)list.size();
+        list.push_back(I | (J << 10) | (K << 20));
+      }
+    h->max_bt_phase = std::max(h->max_bt_phase, (int)list.size() - off[g]);
+  }
+  off[nb] = (int)list.size();
+  for (int I = 0; I < nb; ++I)
+    for (int J = I; J < nb; ++J) tiles.push_back(I | (J << 16));
+  h->nbt = (int)list.size();
+  h->ntiles = (int)tiles.size();
+  h->tile_elems = (int64_t)h->ntiles * B * B;
+  h->zt_elems = (int64_t)h->nbt * 3 * B * B * B;
+  h->bt_list = (int*)dalloc(h, list.size() * sizeof(int));
+  h->bt_off = (int*)dalloc(h, off.size() * sizeof(int));
+  h->bt_rank = (int*)dalloc(h, rank.size() * sizeof(int));
+  h->tile_list = (int*)dalloc(h, tiles.size() * sizeof(int));
+  if (!h->bt_list || !h->bt_off || !h->bt_rank || !h->tile_list) return fail(h, CC_ERR_OOM, "schedule tables");
+  CK(h, cudaMemcpyAsync(h->bt_list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CK(h, cudaMemcpyAsync(h->bt_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CK(h, cudaMemcpyAsync(h->bt_rank, rank.data(), rank.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CK(h, cudaMemcpyAsync(h->tile_list, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CK(h, cudaStreamSynchronize(h->st));  // host vectors go out of scope
+  return CC_OK;
+}
+
+int ensure_stage(cc_handle* h, int64_t elems) {
+  if (h->stage_elems >= elems) return CC_OK;
+  dfree(h, h->stage);
+  h->stage = (double*)dalloc(h, (size_t)elems * sizeof(double));
+  h->stage_elems = h->stage ? elems : 0;
+  return h->stage ? CC_OK : fail(h, CC_ERR_OOM, "staging buffer");
+}
+
+int read_ctl_error(cc_handle* h) {
+  Ctl c;
+  CK(h, cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  if (c.err != 0) {
+    CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    char buf[160];
+    snprintf(buf, sizeof buf, "grid barrier time limit hit in phase %d of a sweep; the state is undefined",
+             c.err_phase);
+    return fail(h, c.err, buf);
+  }
+  return CC_OK;
+}
+
+template <typename T>
+int init_state(cc_handle* h) {
+  const int th = 256;
+  k_fill<T><<<grid_for(h, h->tile_elems, th), th, 0, h->st>>>((T*)h->x, h->tile_elems, T(0));
+  k_fill<T><<<grid_for(h, h->tile_elems, th), th, 0, h->st>>>((T*)h->f, h->tile_elems, (T)(-1.0 / h->o.eps));
+  CK(h, cudaMemsetAsync(h->zt, 0, (size_t)h->zt_elems * sizeof(T), h->st));
+  CK(h, cudaMemsetAsync(h->zp, 0, (size_t)h->ntiles * 2 * h->B * h->B * sizeof(T), h->st));
+  CK(h, cudaGetLastError());
+  return CC_OK;
+}
+
+int create_common(cc_handle** out, int64_t n, const double* d_dev, const double* w_dev, const cc_opts* opts,
+                  cc_handle* h) {
+  h->n = n;
+  h->P = ch2(n);
+  h->T3 = ch3(n);
+  h->B = h->o.tile;
+  h->nb = (int)((n + h->B - 1) / h->B);
+  if (h->nb > 1023) return fail(h, CC_ERR_ARG, "n / tile exceeds 1023 blocks");
+  (void)opts;
+  // validate inputs on device
+  int* flags = (int*)dalloc(h, 4 * sizeof(int));
+  if (!flags) return fail(h, CC_ERR_OOM, "flags");
+  CK(h, cudaMemsetAsync(flags, 0, 4 * sizeof(int), h->st));
+  k_validate<<<grid_for(h, h->P, 256), 256, 0, h->st>>>(d_dev, w_dev, h->P, flags);
+  int hf[4];
+  CK(h, cudaMemcpyAsync(hf, flags, sizeof hf, cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  dfree(h, flags);
+  if (hf[0]) return fail(h, CC_ERR_ARG, "d has non-finite entries");
+  if (hf[1]) return fail(h, CC_ERR_ARG, "w must be finite and > 0");
+  h->unitw = hf[2] == 0;
+  int rc = build_tables(h);
+  if (rc) return rc;
+  h->fp32 = h->o.precision == CC_PREC_FP32_REFINE;
+  h->esz = h->fp32 ? 4 : 8;
+  const size_t te = (size_t)h->tile_elems;
+  h->x = dalloc(h, te * h->esz);
+  h->f = dalloc(h, te * h->esz);
+  h->d = dalloc(h, te * h->esz);
+  h->winv = dalloc(h, te * h->esz);
+  h->zp = dalloc(h, te * 2 * h->esz);
+  h->zt = dalloc(h, (size_t)h->zt_elems * h->esz);
+  h->ctl = (Ctl*)dalloc(h, sizeof(Ctl));
+  h->part_cap = std::max(8 * h->sms, 64);
+  h->part = (double*)dalloc(h, (size_t)h->part_cap * 6 * sizeof(double));  // maxima, then 5 sums each
+  if (!h->x || !h->f || !h->d || !h->winv || !h->zp || !h->zt || !h->ctl || !h->part)
+    return fail(h, CC_ERR_OOM, "device state");
+  CK(h, cudaMallocHost((void**)&h->h_pin, 64 * sizeof(double)));
+  CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->st));
+  CK(h, cudaMemsetAsync(h->d, 0, te * h->esz, h->st));
+  if (h->fp32) {
+    k_fill<float><<<grid_for(h, te, 256), 256, 0, h->st>>>((float*)h->winv, te, 1.0f);
+    k_load_problem<float><<<grid_for(h, h->P, 256), 256, 0, h->st>>>(d_dev, w_dev, (int)n, h->nb, h->B,
+                                                                      (float*)h->d, (float*)h->winv);
+    rc = init_state<float>(h);
+  } else {
+    k_fill<double><<<grid_for(h, te, 256), 256, 0, h->st>>>((double*)h->winv, te, 1.0);
+    k_load_problem<double><<<grid_for(h, h->P, 256), 256, 0, h->st>>>(d_dev, w_dev, (int)n, h->nb, h->B,
+                                                                       (double*)h->d, (double*)h->winv);
+    rc = init_state<double>(h);
+  }
+  if (rc) return rc;
+  CK(h, cudaEventCreate(&h->ev0));
+  CK(h, cudaEventCreate(&h->ev1));
+  rc = configure_sweep(h);
+  if (rc) return rc;
+  CK(h, cudaStreamSynchronize(h->st));
+  *out = h;
+  return CC_OK;
+}
+
+int check_opts(const cc_opts& o) {
+  if (!(o.eps > 0.0) || !std::isfinite(o.eps)) return fail(nullptr, CC_ERR_ARG, "eps must be finite and > 0");
+  if (o.tile != 8 && o.tile != 16 && o.tile != 32) return fail(nullptr, CC_ERR_ARG, "tile must be 8, 16 or 32");
+  if (o.schedule != CC_SCHED_TILED)
+    return fail(nullptr, CC_ERR_UNSUPPORTED, "only the tiled schedule is served by this build");
+  if (o.precision != CC_PREC_FP64 && o.precision != CC_PREC_FP32_REFINE)
+    return fail(nullptr, CC_ERR_ARG, "unknown precision");
+  if (o.exact && o.precision != CC_PREC_FP64) return fail(nullptr, CC_ERR_ARG, "exact mode needs FP64");
+  if (o.check_every < 1) return fail(nullptr, CC_ERR_ARG, "check_every must be >= 1");
+  if (!(o.barrier_timeout_s > 0.0)) return fail(nullptr, CC_ERR_ARG, "barrier_timeout_s must be > 0");
+  if ((o.alloc == nullptr) != (o.free == nullptr)) return fail(nullptr, CC_ERR_ARG, "alloc and free go together");
+  return CC_OK;
+}
+
+int new_handle(cc_handle** out, int64_t n, const cc_opts* opts, cc_handle** hp) {
+  if (!out) return fail(nullptr, CC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 3) return fail(nullptr, CC_ERR_ARG, "n must be >= 3");
+  if (n > 100000) return fail(nullptr, CC_ERR_ARG, "n too large");
+  cc_opts o;
+  cc_opts_default(&o);
+  if (opts) o = *opts;
+  int rc = check_opts(o);
+  if (rc) return rc;
+  cc_handle* h = new (std::nothrow) cc_handle();
+  if (!h) return fail(nullptr, CC_ERR_OOM, "handle");
+  h->o = o;
+  h->st = (cudaStream_t)o.stream;
+  h->dev = o.device;
+  cudaError_t e = cudaSetDevice(h->dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(nullptr, CC_ERR_CUDA, std::string("device: ") + cudaGetErrorString(e));
+  }
+  *hp = h;
+  return CC_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" {
+
+void cc_opts_default(cc_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->eps = 0.2;
+  o->schedule = CC_SCHED_TILED;
+  o->tile = 16;
+  o->precision = CC_PREC_FP64;
+  o->exact = 0;
+  o->check_every = 10;
+  o->device = 0;
+  o->barrier_timeout_s = 2.0;
+  o->stream = nullptr;
+  o->alloc = nullptr;
+  o->free = nullptr;
+  o->alloc_ctx = nullptr;
+  o->grid = 0;
+  o->debug_skip_cta = -1;
+}
+
+int cc_create_device(cc_handle** out, int64_t n, const double* d_dev, const double* w_dev, const cc_opts* opts) {
+  cc_handle* h = nullptr;
+  int rc = new_handle(out, n, opts, &h);
+  if (rc) return rc;
+  if (!d_dev || !w_dev) {
+    cc_destroy(h);
+    return fail(nullptr, CC_ERR_ARG, "d or w is NULL");
+  }
+  rc = create_common(out, n, d_dev, w_dev, opts, h);
+  if (rc) {
+    g_create_error = h->err;
+    cc_destroy(h);
+    *out = nullptr;
+  }
+  return rc;
+}
+
+int cc_create(cc_handle** out, int64_t n, const double* d, const double* w, const cc_opts* opts) {
+  cc_handle* h = nullptr;
+  int rc = new_handle(out, n, opts, &h);
+  if (rc) return rc;
+  if (!d || !w) {
+    cc_destroy(h);
+    return fail(nullptr, CC_ERR_ARG, "d or w is NULL");
+  }
+  const int64_t P = ch2(n);
+  double* buf = (double*)dalloc(h, (size_t)P * 2 * sizeof(double));
+  if (!buf) {
+    cc_destroy(h);
+    return fail(nullptr, CC_ERR_OOM, "input staging");
+  }
+  cudaError_t e = cudaMemcpyAsync(buf, d, P * sizeof(double), cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(buf + P, w, P * sizeof(double), cudaMemcpyHostToDevice, h->st);
+  if (e != cudaSuccess) {
+    cc_destroy(h);
+    return fail(nullptr, CC_ERR_CUDA, std::string("input upload: ") + cudaGetErrorString(e));
+  }
+  rc = create_common(out, n, buf, buf + P, opts, h);
+  if (rc) {
+    g_create_error = h->err;
+    cc_destroy(h);
+    *out = nullptr;
+    return rc;
+  }
+  dfree(h, buf);
+  return CC_OK;
+}
+
+int cc_sweep(cc_handle* h, int64_t k) {
+  if (!h) return fail(nullptr, CC_ERR_ARG, "handle is NULL");
+  if (k < 0) return fail(h, CC_ERR_ARG, "k must be >= 0");
+  CK(h, cudaSetDevice(h->dev));
+  for (int64_t s = 0; s < k; ++s) {
+    const bool last = (s == k - 1);
+    if (last) CK(h, cudaEventRecord(h->ev0, h->st));
+    int rc = launch_sweep(h);
+    if (rc) return rc;
+    if (last) {
+      CK(h, cudaEventRecord(h->ev1, h->st));
+      h->ev_recorded = true;
+    }
+    h->sweeps++;
+  }
+  return CC_OK;
+}
+
+int cc_check(cc_handle* h, cc_stats* st) {
+  if (!h) return fail(nullptr, CC_ERR_ARG, "handle is NULL");
+  CK(h, cudaSetDevice(h->dev));
+  int rc = read_ctl_error(h);
+  if (rc) return rc;
+  const int B = h->B;
+  const int gtri = std::min(h->part_cap, h->sms * 4);
+  const int gpair = std::min(h->part_cap, grid_for(h, h->tile_elems, 256));
+  double* pm = h->part;                        // gtri maxima
+  double* ps = h->part + h->part_cap;          // gpair x 5 sums
+  const double yscale = h->o.exact ? 1.0 : h->o.eps;
+#define LAUNCH_CHECK(T, BV)                                                                                   \
+  k_maxviol_tiled<T, BV><<<gtri, threads_for_tile(BV), 0, h->st>>>((const T*)h->x, (int)h->n, h->nb,      \
+                                                                    h->bt_list, h->nbt, pm);                \
+  k_pairsums_tiled<T, BV><<<gpair, 256, 0, h->st>>>((const T*)h->x, (const T*)h->f, (const T*)h->d,        \
+                                                    (const T*)h->winv, (const T*)h->zp, h->tile_list,      \
+                                                    h->ntiles, (int)h->n, yscale, ps);
+  if (h->fp32) {
+    if (B == 8) { LAUNCH_CHECK(float, 8) } else if (B == 16) { LAUNCH_CHECK(float, 16) } else { LAUNCH_CHECK(float, 32) }
+  } else {
+    if (B == 8) { LAUNCH_CHECK(double, 8) } else if (B == 16) { LAUNCH_CHECK(double, 16) } else { LAUNCH_CHECK(double, 32) }
+  }
+#undef LAUNCH_CHECK
+  CK(h, cudaGetLastError());
+  std::vector<double> hm(gtri), hs((size_t)gpair * 5);
+  CK(h, cudaMemcpyAsync(hm.data(), pm, gtri * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaMemcpyAsync(hs.data(), ps, (size_t)gpair * 5 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  double mv = 0, lp = 0, wf = 0, quad = 0, by = 0, pv = 0;
+  for (int i = 0; i < gtri; ++i) mv = std::max(mv, hm[i]);
+  for (int i = 0; i < gpair; ++i) {
+    lp += hs[5 * i];
+    wf += hs[5 * i + 1];
+    quad += hs[5 * i + 2];
+    by += hs[5 * i + 3];
+    pv = std::max(pv, hs[5 * i + 4]);
+  }
+  cc_stats& s = h->last;
+  s.sweeps = h->sweeps;
+  s.max_violation = mv;
+  s.pair_violation = pv;
+  s.lp_objective = lp;
+  s.wf = wf;
+  s.qp_primal = wf + 0.5 * h->o.eps * quad;
+  s.dual_objective = -by - 0.5 * h->o.eps * quad;
+  s.gap = s.qp_primal - s.dual_objective;
+  if (h->ev_recorded) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) s.last_sweep_ms = ms;
+  }
+  if (st) *st = s;
+  return CC_OK;
+}
+
+int cc_solve(cc_handle* h, double tol, int64_t max_sweeps, int64_t* sweeps_done) {
+  if (!h) return fail(nullptr, CC_ERR_ARG, "handle is NULL");
+  if (!std::isfinite(tol) || tol < 0) return fail(h, CC_ERR_ARG, "tol must be finite and >= 0");
+  if (max_sweeps < 0) return fail(h, CC_ERR_ARG, "max_sweeps must be >= 0");
+  int64_t done = 0;
+  if (sweeps_done) *sweeps_done = 0;
+  while (done < max_sweeps) {
+    int64_t k = std::min<int64_t>(h->o.check_every, max_sweeps - done);
+    int rc = cc_sweep(h, k);
+    if (rc) return rc;
+    done += k;
+    if (sweeps_done) *sweeps_done = done;
+    cc_stats s;
+    rc = cc_check(h, &s);
+    if (rc) return rc;
+    if (s.max_violation <= tol) return CC_OK;
+  }
+  return fail(h, CC_ERR_NOT_CONVERGED, "max_sweeps reached before the tolerance");
+}
+
+int cc_get_x(cc_handle* h, double* x, double* f) {
+  if (!h) return fail(nullptr, CC_ERR_ARG, "handle is NULL");
+  if (!x && !f) return fail(h, CC_ERR_ARG, "x and f are both NULL");
+  CK(h, cudaSetDevice(h->dev));
+  int rc = read_ctl_error(h);
+  if (rc) return rc;
+  rc = ensure_stage(h, 2 * h->P);
+  if (rc) return rc;
+  double* sx = h->stage;
+  double* sf = h->stage + h->P;
+  const int g = grid_for(h, h->P, 256);
+  if (h->fp32)
+    k_pairs_layout<float><<<g, 256, 0, h->st>>>((float*)h->x, (float*)h->f, (int)h->n, h->nb, h->B, sx, sf, 0);
+  else
+    k_pairs_layout<double><<<g, 256, 0, h->st>>>((double*)h->x, (double*)h->f, (int)h->n, h->nb, h->B, sx, sf, 0);
+  CK(h, cudaGetLastError());
+  if (x) CK(h, cudaMemcpyAsync(x, sx, h->P * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  if (f) CK(h, cudaMemcpyAsync(f, sf, h->P * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  return CC_OK;
+}
+
+static int move_duals(cc_handle* h, double* y_tri, double* y_pair, int64_t first, int64_t count, int dir) {
+  const double scale = h->o.exact ? 1.0 : h->o.eps;
+  const int64_t chunk = std::min<int64_t>(std::max<int64_t>(count, 1), (int64_t)1 << 22);
+  int rc = ensure_stage(h, std::max<int64_t>(3 * chunk, 2 * h->P));
+  if (rc) return rc;
+  if (y_tri) {
+    for (int64_t c0 = 0; c0 < count; c0 += chunk) {
+      const int64_t m = std::min(chunk, count - c0);
+      if (dir == 1)
+        CK(h, cudaMemcpyAsync(h->stage, y_tri + 3 * c0, 3 * m * sizeof(double), cudaMemcpyHostToDevice, h->st));
+      const int g = grid_for(h, m, 256);
+#define LAUNCH_TD(T, BV) \
+  k_tri_duals_tiled<T, BV><<<g, 256, 0, h->st>>>((T*)h->zt, h->bt_rank, (int)h->n, h->nb, first + c0, m, h->stage, scale, dir);
+      if (h->fp32) {
+        if (h->B == 8) { LAUNCH_TD(float, 8) } else if (h->B == 16) { LAUNCH_TD(float, 16) } else { LAUNCH_TD(float, 32) }
+      } else {
+        if (h->B == 8) { LAUNCH_TD(double, 8) } else if (h->B == 16) { LAUNCH_TD(double, 16) } else { LAUNCH_TD(double, 32) }
+      }
+#undef LAUNCH_TD
+      CK(h, cudaGetLastError());
+      if (dir == 0)
+        CK(h, cudaMemcpyAsync(y_tri + 3 * c0, h->stage, 3 * m * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      CK(h, cudaStreamSynchronize(h->st));
+    }
+  }
+  if (y_pair) {
+    if (dir == 1)
+      CK(h, cudaMemcpyAsync(h->stage, y_pair, 2 * h->P * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    const int g = grid_for(h, h->P, 256);
+    if (h->fp32)
+      k_pair_duals_tiled<float><<<g, 256, 0, h->st>>>((float*)h->zp, (int)h->n, h->nb, h->B, h->stage, scale, dir);
+    else
+      k_pair_duals_tiled<double><<<g, 256, 0, h->st>>>((double*)h->zp, (int)h->n, h->nb, h->B, h->stage, scale, dir);
+    CK(h, cudaGetLastError());
+    if (dir == 0)
+      CK(h, cudaMemcpyAsync(y_pair, h->stage, 2 * h->P * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+  }
+  return CC_OK;
+}
+
+int cc_get_duals(cc_handle* h, double* y_tri, double* y_pair, int64_t tri_first, int64_t tri_count) {
+  if (!h) return fail(nullptr, CC_ERR_ARG, "handle is NULL");
+  if (y_tri && (tri_first < 0 || tri_count < 0 || tri_first + tri_count > h->T3))
+    return fail(h, CC_ERR_ARG, "triplet range out of bounds");
+  CK(h, cudaSetDevice(h->dev));
+  int rc = read_ctl_error(h);
+  if (rc) return rc;
+  return move_duals(h, y_tri, y_pair, tri_first, tri_count, 0);
+}
+
+int cc_set_state(cc_handle* h, const double* x, const double* f, const double* y_tri, const double* y_pair) {
+  if (!h) return fail(nullptr, CC_ERR_ARG, "handle is NULL");
+  if (!x || !f || !y_tri || !y_pair) return fail(h, CC_ERR_ARG, "all four arrays are required");
+  CK(h, cudaSetDevice(h->dev));
+  int rc = read_ctl_error(h);
+  if (rc) return rc;
+  rc = ensure_stage(h, 2 * h->P);
+  if (rc) return rc;
+  CK(h, cudaMemcpyAsync(h->stage, x, h->P * sizeof(double), cudaMemcpyHostToDevice, h->st));
+  CK(h, cudaMemcpyAsync(h->stage + h->P, f, h->P * sizeof(double), cudaMemcpyHostToDevice, h->st));
+  const int g = grid_for(h, h->P, 256);
+  if (h->fp32)
+    k_pairs_layout<float><<<g, 256, 0, h->st>>>((float*)h->x, (float*)h->f, (int)h->n, h->nb, h->B, h->stage,
+                                                h->stage + h->P, 1);
+  else
+    k_pairs_layout<double><<<g, 256, 0, h->st>>>((double*)h->x, (double*)h->f, (int)h->n, h->nb, h->B, h->stage,
+                                                 h->stage + h->P, 1);
+  CK(h, cudaGetLastError());
+  CK(h, cudaStreamSynchronize(h->st));
+  rc = move_duals(h, const_cast<double*>(y_tri), const_cast<double*>(y_pair), 0, h->T3, 1);
+  if (rc) return rc;
+  h->sweeps = 0;
+  return CC_OK;
+}
+
+int cc_get_stats(cc_handle* h, cc_stats* st) {
+  if (!h || !st) return fail(h, CC_ERR_ARG, "NULL argument");
+  *st = h->last;
+  st->sweeps = h->sweeps;
+  return CC_OK;
+}
+
+int64_t cc_device_bytes(const cc_handle* h) { return h ? h->dev_bytes : 0; }
+
+void cc_destroy(cc_handle* h) {
+  if (!h) return;
+  cudaSetDevice(h->dev);
+  if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
+  while (!h->allocs.empty()) dfree(h, h->allocs.back().p);
+  if (h->h_pin) cudaFreeHost(h->h_pin);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  delete h;
+}
+
+const char* cc_last_error(const cc_handle* h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+}  // extern "C"

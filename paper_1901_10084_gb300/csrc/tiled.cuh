@@ -1,0 +1,381 @@
+// Tiled schedule: sweep, convergence-check and layout kernels.
+//
+// The index set is cut into blocks of B consecutive objects (Nb = ceil(n/B)
+// blocks).  x, f, d and W^{-1} live in B x B tiles (I,J), I<=J, of the strict
+// upper triangle, each tile contiguous (tile_index order), so that a CTA moves
+// whole tiles between HBM/L2 and shared memory (the b x b tiles of Sec. III-C).
+//
+// A sweep is one cooperative launch.  Phase g = 0..Nb-1 holds the block triples
+// I<=J<=K with (I+J+K) mod Nb = g; two of them share at most one block, so they
+// touch disjoint tiles and run on different CTAs without locks (the two-triplet
+// lemma of Sec. III-A lifted to blocks).  Inside a block triple the CTA walks
+// sub-phases t = 0..B-1; sub-phase t holds the local offsets (a,b,c) with
+// (a+b+c) mod B = t, and any two of those share at most one global index, so
+// one sub-phase runs with one triplet per thread on tiles held in shared memory.
+// A bounded grid barrier separates phases; the pair rows run after the last one.
+//
+// Triangle duals are stored in schedule order: block triple w (its rank in the
+// concatenated phase lists) owns 3 B^3 slots, sub-phase-major, then row, then
+// local slot a*B+b, so each thread's three duals of a sub-phase sit at a fixed
+// stride and consecutive threads read consecutive words.
+#pragma once
+#include "common.cuh"
+
+namespace ccd {
+
+template <int B>
+struct TileCfg {
+  static constexpr int BB = B * B;
+  static constexpr int NT = BB < 256 ? BB : 256;   // threads per CTA
+  static constexpr int SPT = BB / NT;              // slots per thread and sub-phase
+};
+
+template <typename T>
+struct TiledArgs {
+  int n, nb, ntiles;
+  T* x;                 // tile-major distances
+  T* f;                 // tile-major slacks
+  const T* d;           // tile-major dissimilarities
+  const T* winv;        // tile-major 1/w
+  T* zt;                // triangle duals, 3 B^3 per block triple
+  T* zp;                // pair duals, 2 B^2 per tile (row +, row -)
+  const int* bt_list;   // block triples in schedule order, packed I | J<<10 | K<<20
+  const int* bt_off;    // nb+1 offsets of the phases in bt_list
+  const int* tile_list; // tiles in tile_index order, packed I | J<<16
+  Ctl* ctl;
+  long long timeout_ns;
+  T eps;                // eps of Eq. (qp)
+  T r_unit;             // 1/3: 1/(a^T W^{-1} a) for unit weights
+  int skip_cta;         // fault-injection hook (-1 = off)
+};
+
+__device__ __forceinline__ void unpack_bt(int pk, int& I, int& J, int& K) {
+  I = pk & 1023;
+  J = (pk >> 10) & 1023;
+  K = (pk >> 20) & 1023;
+}
+
+// Project every triplet of block triple number w (schedule rank).
+template <typename T, bool EXACT, bool UNITW, int B>
+__device__ __forceinline__ void tiled_block_triple(const TiledArgs<T>& a, int w, T* s0, T* s1,
+                                                   T* s2, T* q0, T* q1, T* q2) {
+  using C = TileCfg<B>;
+  int I, J, K;
+  unpack_bt(a.bt_list[w], I, J, K);
+  const int64_t oIJ = tile_index(a.nb, I, J) * C::BB;
+  const int64_t oIK = tile_index(a.nb, I, K) * C::BB;
+  const int64_t oJK = tile_index(a.nb, J, K) * C::BB;
+  const bool kj = (K == J), ij = (I == J);
+  // tile (I,K) is tile (I,J) when K == J; tile (J,K) is tile (I,K) when I == J
+  T* pIJ = s0;
+  T* pIK = kj ? s0 : s1;
+  T* pJK = ij ? pIK : s2;
+  T* wIJ = q0;
+  T* wIK = kj ? q0 : q1;
+  T* wJK = ij ? wIK : q2;
+  for (int e = threadIdx.x; e < C::BB; e += C::NT) {
+    s0[e] = ld_l2(a.x + oIJ + e);
+    if (!kj) s1[e] = ld_l2(a.x + oIK + e);
+    if (!ij) s2[e] = ld_l2(a.x + oJK + e);
+    if (!UNITW) {
+      q0[e] = a.winv[oIJ + e];
+      if (!kj) q1[e] = a.winv[oIK + e];
+      if (!ij) q2[e] = a.winv[oJK + e];
+    }
+  }
+  __syncthreads();
+  T* zb = a.zt + (int64_t)w * (3 * B * C::BB);
+  const int kB = K * B;
+  for (int t = 0; t < B; ++t) {
+    T* zs = zb + (int64_t)t * (3 * C::BB);
+#pragma unroll
+    for (int q = 0; q < C::SPT; ++q) {
+      const int slot = threadIdx.x + q * C::NT;
+      const int la = slot / B, lb = slot % B;
+      const int lc = (t - la - lb) & (B - 1);
+      const bool valid = (!ij || la < lb) && (!kj || lb < lc) && (kB + lc < a.n);
+      if (valid) {
+        T z0 = ld_stream(zs + slot);
+        T z1 = ld_stream(zs + C::BB + slot);
+        T z2 = ld_stream(zs + 2 * C::BB + slot);
+        const int eij = la * B + lb, eik = la * B + lc, ejk = lb * B + lc;
+        T xij = pIJ[eij], xik = pIK[eik], xjk = pJK[ejk];
+        T vij = T(1), vik = T(1), vjk = T(1);
+        if (!UNITW) {
+          vij = wIJ[eij];
+          vik = wIK[eik];
+          vjk = wJK[ejk];
+        }
+        triplet_rows<T, EXACT, UNITW>(xij, xik, xjk, vij, vik, vjk, a.eps, a.r_unit, z0, z1, z2);
+        pIJ[eij] = xij;
+        pIK[eik] = xik;
+        pJK[ejk] = xjk;
+        st_stream(zs + slot, z0);
+        st_stream(zs + C::BB + slot, z1);
+        st_stream(zs + 2 * C::BB + slot, z2);
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < C::BB; e += C::NT) {
+    a.x[oIJ + e] = s0[e];
+    if (!kj) a.x[oIK + e] = s1[e];
+    if (!ij) a.x[oJK + e] = s2[e];
+  }
+  __syncthreads();
+}
+
+// The two rows of every pair (the last phase of a sweep).
+template <typename T, bool EXACT, int B>
+__device__ __forceinline__ void tiled_pair_phase(const TiledArgs<T>& a) {
+  using C = TileCfg<B>;
+  for (int tl = blockIdx.x; tl < a.ntiles; tl += gridDim.x) {
+    const int pk = a.tile_list[tl];
+    const int I = pk & 0xffff, J = pk >> 16;
+    for (int slot = threadIdx.x; slot < C::BB; slot += C::NT) {
+      const int la = slot / B, lb = slot % B;
+      if ((I < J || la < lb) && J * B + lb < a.n) {
+        const int64_t e = (int64_t)tl * C::BB + slot;
+        T* zq = a.zp + (int64_t)tl * (2 * C::BB) + slot;
+        T x = ld_l2(a.x + e), f = a.f[e];
+        T zp = zq[0], zm = zq[C::BB];
+        pair_rows<T, EXACT>(x, f, a.d[e], a.winv[e], a.eps, zp, zm);
+        a.x[e] = x;
+        a.f[e] = f;
+        zq[0] = zp;
+        zq[C::BB] = zm;
+      }
+    }
+  }
+}
+
+template <typename T, bool EXACT, bool UNITW, int B>
+__global__ void __launch_bounds__(TileCfg<B>::NT) k_sweep_tiled(TiledArgs<T> a) {
+  using C = TileCfg<B>;
+  __shared__ T sx[3][C::BB];
+  __shared__ T sw[UNITW ? 1 : 3][C::BB];
+  __shared__ int s_flag;
+  unsigned target = 0;
+  for (int g = 0; g < a.nb; ++g) {
+    const int beg = a.bt_off[g], end = a.bt_off[g + 1];
+    for (int w = beg + (int)blockIdx.x; w < end; w += gridDim.x)
+      tiled_block_triple<T, EXACT, UNITW, B>(a, w, sx[0], sx[1], sx[2], sw[0], sw[UNITW ? 0 : 1],
+                                             sw[UNITW ? 0 : 2]);
+    target += gridDim.x;
+    const bool skip = (g == 0) && ((int)blockIdx.x == a.skip_cta);
+    if (!grid_barrier(a.ctl, target, a.timeout_ns, g, skip, &s_flag)) return;
+  }
+  tiled_pair_phase<T, EXACT, B>(a);
+}
+
+// ------------------------------------------------------------ reductions
+
+template <typename V, typename Op>
+__device__ __forceinline__ V block_reduce(V v, Op op, V* sred, V identity) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) sred[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < nw ? sred[lane] : identity;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;  // valid in thread 0
+}
+
+struct MaxOp {
+  __device__ double operator()(double a, double b) const { return fmax(a, b); }
+};
+struct SumOp {
+  __device__ double operator()(double a, double b) const { return a + b; }
+};
+
+// Largest metric-row violation max(0, x_h - x_a - x_b) over all triplets,
+// evaluated in FP64; one partial maximum per CTA.
+template <typename T, int B>
+__global__ void __launch_bounds__(TileCfg<B>::NT) k_maxviol_tiled(const T* __restrict__ x, int n, int nb,
+                                                                   const int* __restrict__ bt_list, int nbt,
+                                                                   double* part) {
+  using C = TileCfg<B>;
+  __shared__ T sx[3][C::BB];
+  __shared__ double sred[32];
+  double m = 0.0;
+  for (int w = blockIdx.x; w < nbt; w += gridDim.x) {
+    int I, J, K;
+    unpack_bt(bt_list[w], I, J, K);
+    const int64_t oIJ = tile_index(nb, I, J) * C::BB, oIK = tile_index(nb, I, K) * C::BB,
+                  oJK = tile_index(nb, J, K) * C::BB;
+    for (int e = threadIdx.x; e < C::BB; e += C::NT) {
+      sx[0][e] = x[oIJ + e];
+      sx[1][e] = x[oIK + e];
+      sx[2][e] = x[oJK + e];
+    }
+    __syncthreads();
+    const bool kj = (K == J), ij = (I == J);
+    const int kB = K * B;
+    for (int slot = threadIdx.x; slot < C::BB; slot += C::NT) {
+      const int la = slot / B, lb = slot % B;
+      if (ij && la >= lb) continue;
+      const double xij = (double)sx[0][la * B + lb];
+      for (int lc = kj ? lb + 1 : 0; lc < B && kB + lc < n; ++lc) {
+        const double xik = (double)sx[1][la * B + lc], xjk = (double)sx[2][lb * B + lc];
+        const double v0 = (xij - xik) - xjk, v1 = (xik - xij) - xjk, v2 = (xjk - xij) - xik;
+        m = fmax(m, fmax(v0, fmax(v1, v2)));
+      }
+    }
+    __syncthreads();
+  }
+  m = block_reduce(m, MaxOp(), sred, 0.0);
+  if (threadIdx.x == 0) part[blockIdx.x] = m;
+}
+
+// Pair sums: lp = sum w|x-d|, wf = sum w f, quad = sum w (x^2 + f^2),
+// by = sum d (y+ - y-) (y = yscale * stored dual), pv = max pair violation.
+template <typename T, int B>
+__global__ void __launch_bounds__(256) k_pairsums_tiled(const T* __restrict__ x, const T* __restrict__ f,
+                                                         const T* __restrict__ d, const T* __restrict__ winv,
+                                                         const T* __restrict__ zp, const int* __restrict__ tile_list,
+                                                         int ntiles, int n, double yscale, double* part) {
+  using C = TileCfg<B>;
+  __shared__ double sred[32];
+  double lp = 0, wf = 0, quad = 0, by = 0, pv = 0;
+  const int64_t total = (int64_t)ntiles * C::BB;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int tl = (int)(e / C::BB), slot = (int)(e % C::BB);
+    const int pk = tile_list[tl];
+    const int I = pk & 0xffff, J = pk >> 16;
+    const int la = slot / B, lb = slot % B;
+    if (!((I < J || la < lb) && J * B + lb < n)) continue;
+    const double xv = x[e], fv = f[e], dv = d[e], wv = 1.0 / (double)winv[e];
+    const double yp = yscale * (double)zp[(int64_t)tl * 2 * C::BB + slot];
+    const double ym = yscale * (double)zp[(int64_t)tl * 2 * C::BB + C::BB + slot];
+    lp += wv * fabs(xv - dv);
+    wf += wv * fv;
+    quad += wv * (xv * xv + fv * fv);
+    by += dv * (yp - ym);
+    pv = fmax(pv, fmax(xv - fv - dv, dv - xv - fv));
+  }
+  lp = block_reduce(lp, SumOp(), sred, 0.0);
+  if (threadIdx.x == 0) part[5 * blockIdx.x + 0] = lp;
+  wf = block_reduce(wf, SumOp(), sred, 0.0);
+  if (threadIdx.x == 0) part[5 * blockIdx.x + 1] = wf;
+  quad = block_reduce(quad, SumOp(), sred, 0.0);
+  if (threadIdx.x == 0) part[5 * blockIdx.x + 2] = quad;
+  by = block_reduce(by, SumOp(), sred, 0.0);
+  if (threadIdx.x == 0) part[5 * blockIdx.x + 3] = by;
+  pv = block_reduce(pv, MaxOp(), sred, 0.0);
+  if (threadIdx.x == 0) part[5 * blockIdx.x + 4] = fmax(pv, 0.0);
+}
+
+// ------------------------------------------------------------ layout moves
+
+// packed pair p -> (i, j)
+__device__ __forceinline__ void pair_unrank(int64_t n, int64_t p, int& i, int& j) {
+  int lo = 0, hi = (int)n - 2;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (pair_index(n, mid, mid + 1) <= p) lo = mid; else hi = mid - 1;
+  }
+  i = lo;
+  j = (int)(p - pair_index(n, i, i + 1)) + i + 1;
+}
+
+// dir 0: tile-major (x, f) -> packed double buffers; dir 1: the reverse.
+template <typename T>
+__global__ void k_pairs_layout(T* x, T* f, int n, int nb, int B, double* px, double* pf, int dir) {
+  const int64_t P = ch2(n);
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+    int i, j;
+    pair_unrank(n, p, i, j);
+    const int64_t e = tiled_offset(nb, B, i, j);
+    if (dir == 0) {
+      if (px) px[p] = (double)x[e];
+      if (pf) pf[p] = (double)f[e];
+    } else {
+      if (px) x[e] = (T)px[p];
+      if (pf) f[e] = (T)pf[p];
+    }
+  }
+}
+
+// Packed d, w (device, double) -> tile-major d and W^{-1}.
+template <typename T>
+__global__ void k_load_problem(const double* pd, const double* pw, int n, int nb, int B, T* d, T* winv) {
+  const int64_t P = ch2(n);
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+    int i, j;
+    pair_unrank(n, p, i, j);
+    const int64_t e = tiled_offset(nb, B, i, j);
+    d[e] = (T)pd[p];
+    winv[e] = (T)(1.0 / pw[p]);
+  }
+}
+
+// Input checks on device: flags[0] += non-finite d, flags[1] += w not finite
+// or <= 0, flags[2] += w != 1.
+__global__ void k_validate(const double* pd, const double* pw, int64_t P, int* flags) {
+  int bad_d = 0, bad_w = 0, nonunit = 0;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+    const double dv = pd[p], wv = pw[p];
+    bad_d |= !isfinite(dv);
+    bad_w |= !(isfinite(wv) && wv > 0.0);
+    nonunit |= (wv != 1.0);
+  }
+  if (__syncthreads_or(bad_d) && threadIdx.x == 0) atomicAdd(&flags[0], 1);
+  if (__syncthreads_or(bad_w) && threadIdx.x == 0) atomicAdd(&flags[1], 1);
+  if (__syncthreads_or(nonunit) && threadIdx.x == 0) atomicAdd(&flags[2], 1);
+}
+
+template <typename T>
+__global__ void k_fill(T* p, int64_t count, T v) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+    p[e] = v;
+}
+
+// Triangle duals between the tiled store and canonical order.
+// dir 0: buf[3q + r] = scale * z;  dir 1: z = buf[3q + r] / scale.
+template <typename T, int B>
+__global__ void k_tri_duals_tiled(T* zt, const int* bt_rank, int n, int nb, int64_t first, int64_t count,
+                                  double* buf, double scale, int dir) {
+  constexpr int BB = B * B;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    tri_unrank(n, first + q, i, j, k);
+    const int I = i / B, J = j / B, K = k / B;
+    const int la = i % B, lb = j % B, lc = k % B;
+    const int t = (la + lb + lc) % B;
+    const int64_t w = bt_rank[((int64_t)I * nb + J) * nb + K];
+    const int64_t base = w * (3 * B * BB) + (int64_t)t * (3 * BB) + la * B + lb;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      if (dir == 0) buf[3 * q + r] = scale * (double)zt[base + r * BB];
+      else zt[base + r * BB] = (T)(buf[3 * q + r] / scale);
+    }
+  }
+}
+
+// Pair duals between the tiled store and packed order (2 per pair).
+template <typename T>
+__global__ void k_pair_duals_tiled(T* zp, int n, int nb, int B, double* buf, double scale, int dir) {
+  const int64_t P = ch2(n);
+  const int BB = B * B;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+    int i, j;
+    pair_unrank(n, p, i, j);
+    const int64_t tl = tile_index(nb, i / B, j / B);
+    const int64_t e = tl * (2 * BB) + (i % B) * B + (j % B);
+    if (dir == 0) {
+      buf[2 * p] = scale * (double)zp[e];
+      buf[2 * p + 1] = scale * (double)zp[e + BB];
+    } else {
+      zp[e] = (T)(buf[2 * p] / scale);
+      zp[e + BB] = (T)(buf[2 * p + 1] / scale);
+    }
+  }
+}
+
+}  // namespace ccd

@@ -1,0 +1,68 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads
+and exports every function include/ccdyk.h declares, and argument checks
+that run before any device call reject bad options."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ccdyk.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cc_[a-z_]+)\s*\(", src)) - {"cc_alloc_fn", "cc_free_fn"})
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1901_10084_gb300 import build, _native
+    build()
+    return _native.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+    from paper_1901_10084_gb300 import _native
+    assert set(_native.EXPORTS) <= set(names)
+
+
+def test_opts_defaults(lib):
+    from paper_1901_10084_gb300 import _native as N
+    o = N.cc_opts_default()
+    assert o.eps == 0.2 and o.schedule == N.CC_SCHED_TILED and o.tile == 16
+    assert o.precision == N.CC_PREC_FP64 and o.check_every == 10 and o.debug_skip_cta == -1
+
+
+@pytest.mark.parametrize("field,value", [("eps", 0.0), ("eps", -1.0), ("eps", float("inf")),
+                                         ("tile", 12), ("check_every", 0),
+                                         ("barrier_timeout_s", 0.0), ("precision", 7)])
+def test_bad_options_rejected_before_device_work(lib, field, value):
+    import numpy as np
+    from paper_1901_10084_gb300 import _native as N
+    o = N.cc_opts_default()
+    setattr(o, field, value)
+    with pytest.raises(N.CCError) as e:
+        N.cc_create(10, np.zeros(45), np.ones(45), o)
+    assert e.value.code == N.CC_ERR_ARG
+    assert N.cc_last_error(None)
+
+
+def test_small_n_rejected(lib):
+    import numpy as np
+    from paper_1901_10084_gb300 import _native as N
+    with pytest.raises(N.CCError) as e:
+        N.cc_create(2, np.zeros(1), np.ones(1), None)
+    assert e.value.code == N.CC_ERR_ARG
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    from paper_1901_10084_gb300 import _native as N
+    assert lib.cc_sweep(None, 1) == N.CC_ERR_ARG
+    assert lib.cc_check(None, None) == N.CC_ERR_ARG
+    lib.cc_destroy(None)

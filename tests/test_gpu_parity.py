@@ -1,0 +1,235 @@
+"""GPU path against the oracle on the same seeded inputs (through the C ABI).
+
+Tolerances: the exact mode evaluates every row operation by operation in
+IEEE double in the oracle's rounding order, so it must agree bit for bit.
+The fused form differs from the oracle only in rounding: one sweep from an
+identical state must agree to 1e-12 in the norm
+||gpu - oracle||_inf / max(||oracle||_inf, 1) on x, f and y; at convergence
+the LP objective must agree to 1e-6 relative and the violation be <= 1e-4.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from instances import planted_partition, chung_lu, clustered, workload
+
+pytestmark = pytest.mark.gpu
+
+TOL_SWEEP = 1e-12
+
+
+def _solver(n, d, w, **kw):
+    import paper_1901_10084_gb300 as cc
+    return cc.Solver(n, d, w, **kw)
+
+
+def _gpu_state(s):
+    x, f = s.get_x()
+    yt, yp = s.get_duals()
+    return x, f, yt, yp
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1.0)) if a.size else 0.0
+
+
+def _assert_state_close(g, o, tol):
+    x, f, yt, yp = g
+    assert _rel(x, o.x) <= tol
+    assert _rel(f, o.f) <= tol
+    assert _rel(yt, o.ytri) <= tol
+    assert _rel(yp, o.ypair) <= tol
+
+
+def _assert_state_equal(g, o):
+    x, f, yt, yp = g
+    np.testing.assert_array_equal(x, o.x)
+    np.testing.assert_array_equal(f, o.f)
+    np.testing.assert_array_equal(yt, o.ytri)
+    np.testing.assert_array_equal(yp, o.ypair)
+
+
+# ---------------------------------------------------------------- exact mode
+
+@pytest.mark.parametrize("n,tile,weighted", [(60, 16, False), (60, 8, True), (61, 16, True),
+                                             (37, 32, False), (3, 8, False), (17, 16, True),
+                                             (100, 8, False)])
+def test_exact_mode_is_bitwise_equal(n, tile, weighted):
+    d, w, _ = planted_partition(n, 4, 0.8, 0.1, seed=n, weights=(0.5, 2.0) if weighted else None)
+    o = oracle.State(n, d, w, 0.2)
+    with _solver(n, d, w, eps=0.2, tile=tile, exact=True) as s:
+        o.sweep(2, tile)
+        s.sweep(1)
+        _assert_state_equal(_gpu_state(s), o)
+        o.sweep(2, tile)
+        o.sweep(2, tile)
+        s.sweep(2)
+        _assert_state_equal(_gpu_state(s), o)
+
+
+# ---------------------------------------------------------------- fused form
+
+@pytest.mark.parametrize("n,tile,weighted,pre", [(60, 16, False, 3), (61, 16, True, 5),
+                                                 (200, 16, False, 2), (150, 32, True, 2),
+                                                 (90, 8, True, 4)])
+def test_fused_one_sweep_from_identical_state(n, tile, weighted, pre):
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=n, weights=(0.5, 2.0) if weighted else None)
+    o = oracle.State(n, d, w, 0.2)
+    for _ in range(pre):
+        o.sweep(2, tile)
+    with _solver(n, d, w, eps=0.2, tile=tile) as s:
+        s.set_state(o.x, o.f, o.ytri, o.ypair)
+        _assert_state_close(_gpu_state(s), o, 1e-15)   # round trip of the state
+        s.sweep(1)
+        o.sweep(2, tile)
+        _assert_state_close(_gpu_state(s), o, TOL_SWEEP)
+
+
+def test_fused_matches_over_many_sweeps_planted60():
+    n, d, w, _ = workload("planted60")
+    o = oracle.State(n, d, w, 0.2)
+    with _solver(n, d, w, eps=0.2, tile=16) as s:
+        for _ in range(20):
+            o.sweep(2, 16)
+        s.sweep(20)
+        # errors of the fused form stay at rounding level over many sweeps
+        _assert_state_close(_gpu_state(s), o, 1e-11)
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_converged_objective_planted60(tile):
+    n, d, w, _ = workload("planted60")
+    o = oracle.State(n, d, w, 0.2)
+    ko = o.solve(1e-4, 5000, schedule=2, tile=tile, check_every=1)
+    assert ko > 0
+    with _solver(n, d, w, eps=0.2, tile=tile, check_every=1) as s:
+        conv, kg = s.solve(1e-4, 5000)
+        st = s.check()
+    assert conv and st["max_violation"] <= 1e-4
+    assert kg == ko
+    oo = o.objectives()
+    assert abs(st["lp_objective"] - oo["lp"]) <= 1e-6 * abs(oo["lp"])
+    assert abs(st["qp_primal"] - oo["qp_primal"]) <= 1e-6 * abs(oo["qp_primal"])
+
+
+def test_check_quantities_match_oracle():
+    n = 70
+    d, w, _ = planted_partition(n, 3, 0.7, 0.2, seed=4, weights=(0.5, 2.0))
+    o = oracle.State(n, d, w, 0.3)
+    for _ in range(4):
+        o.sweep(2, 16)
+    with _solver(n, d, w, eps=0.3, tile=16, exact=True) as s:
+        s.sweep(4)
+        st = s.check()
+    oo = o.objectives()
+    assert st["max_violation"] == o.max_violation()        # same x, same arithmetic
+    assert st["pair_violation"] == pytest.approx(oo["pair_violation"], abs=1e-15)
+    for k_gpu, k_ora in (("lp_objective", "lp"), ("qp_primal", "qp_primal"), ("dual_objective", "dual"),
+                         ("wf", "wf")):
+        assert st[k_gpu] == pytest.approx(oo[k_ora], rel=1e-12, abs=1e-12)
+
+
+def test_dual_range_queries():
+    n = 45
+    d, w, _ = planted_partition(n, 3, 0.7, 0.2, seed=2)
+    with _solver(n, d, w, tile=8) as s:
+        s.sweep(3)
+        full, yp = s.get_duals()
+        T = n * (n - 1) * (n - 2) // 6
+        for first, count in ((0, 1), (5, 100), (T - 7, 7), (1234, 3000), (0, 0)):
+            part, _ = s.get_duals(first, count, pairs=False)
+            np.testing.assert_array_equal(part, full[3 * first: 3 * (first + count)])
+
+
+def test_resume_is_exact():
+    """run(k1 + k2) == run(k1); save; restore into a new handle; run(k2)."""
+    n = 50
+    d, w, _ = planted_partition(n, 3, 0.7, 0.2, seed=9, weights=(0.5, 2.0))
+    with _solver(n, d, w, tile=16, exact=True) as a:
+        a.sweep(7)
+        ref = _gpu_state(a)
+    with _solver(n, d, w, tile=16, exact=True) as b:
+        b.sweep(4)
+        snap = _gpu_state(b)
+    with _solver(n, d, w, tile=16, exact=True) as c:
+        c.set_state(*snap)
+        c.sweep(3)
+        got = _gpu_state(c)
+    for g, r in zip(got, ref):
+        np.testing.assert_array_equal(g, r)
+
+
+@pytest.mark.parametrize("n,k,eps", [(300, 6, 0.2), (130, 3, 1.0)])
+def test_closed_form_clustered_on_gpu(n, k, eps):
+    d, w, _ = clustered(n, k, seed=1, weights=(0.5, 2.0))
+    with _solver(n, d, w, eps=eps, tile=16, check_every=5) as s:
+        conv, _ = s.solve(1e-13, 5000)
+        s.sweep(10)
+        x, f = s.get_x()
+        yt, yp = s.get_duals()
+    assert conv
+    np.testing.assert_allclose(x, d, atol=1e-10)
+    np.testing.assert_allclose(f, 0.0, atol=1e-10)
+    np.testing.assert_allclose(yp[0::2], w * (1 - eps * d) / 2, atol=1e-9)
+    np.testing.assert_allclose(yp[1::2], w * (1 + eps * d) / 2, atol=1e-9)
+    assert yt.max() <= 1e-9
+
+
+def test_invalid_inputs_are_rejected():
+    import paper_1901_10084_gb300 as cc
+    n = 10
+    P = n * (n - 1) // 2
+    d, w = np.zeros(P), np.ones(P)
+    bad_w = w.copy()
+    bad_w[3] = 0.0
+    with pytest.raises(cc.CCError) as e:
+        cc.Solver(n, d, bad_w)
+    assert e.value.code == cc.CC_ERR_ARG
+    bad_d = d.copy()
+    bad_d[7] = np.nan
+    with pytest.raises(cc.CCError) as e:
+        cc.Solver(n, bad_d, w)
+    assert e.value.code == cc.CC_ERR_ARG
+
+
+def test_barrier_time_limit_reports_and_context_survives():
+    """One CTA leaves without arriving at the first barrier: the others hit
+    the time limit, the sweep returns, the next check reports
+    CC_ERR_TIMEOUT, and the context keeps working."""
+    import paper_1901_10084_gb300 as cc
+    n = 200
+    d, w, _ = planted_partition(n, 4, 0.8, 0.1, seed=0)
+    with _solver(n, d, w, tile=16, barrier_timeout_s=0.05, debug_skip_cta=0, grid=8) as s:
+        s.sweep(1)
+        with pytest.raises(cc.CCError) as e:
+            s.check()
+        assert e.value.code == cc.CC_ERR_TIMEOUT
+    o = oracle.State(n, d, w, 0.2)
+    o.sweep(2, 16)
+    with _solver(n, d, w, tile=16, exact=True) as s:
+        s.sweep(1)
+        _assert_state_equal(_gpu_state(s), o)
+
+
+# ---------------------------------------------------------------- full size
+
+def test_full_size_chunglu1000_one_sweep():
+    """The benchmark workload (n = 1000, tile 16, default launch): one sweep
+    from the initial state in both forms against the oracle; x and f in full,
+    the duals on three sampled ranges."""
+    n, d, w, _ = workload("chunglu1000")
+    o = oracle.State(n, d, w, 0.2)
+    o.sweep(2, 16)
+    T = n * (n - 1) * (n - 2) // 6
+    ranges = [(0, 200000), (T // 2, 200000), (T - 200000, 200000)]
+    for exact in (True, False):
+        with _solver(n, d, w, eps=0.2, tile=16, exact=exact) as s:
+            s.sweep(1)
+            x, f = s.get_x()
+            tol = 0.0 if exact else TOL_SWEEP
+            assert _rel(x, o.x) <= tol and _rel(f, o.f) <= tol
+            for first, count in ranges:
+                yt, _ = s.get_duals(first, count, pairs=False)
+                assert _rel(yt, o.ytri[3 * first: 3 * (first + count)]) <= tol
+            st = s.check()
+            assert st["max_violation"] == pytest.approx(o.max_violation(), abs=1e-12)
