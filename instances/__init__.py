@@ -97,4 +97,8 @@ def workload(name: str):
     if name == "chunglu3000w":
         d, w, _ = chung_lu(3000, 2.5, 10.0, seed=2, weights=(0.5, 2.0))
         return 3000, d, w, "Chung-Lu n=3000, exponent 2.5, mean degree 10, seed 2, w~U[0.5,2]"
+    if name.startswith("chunglu") and name[7:].isdigit():
+        n = int(name[7:])
+        d, w, _ = chung_lu(n, 2.5, 8.0, seed=1)
+        return n, d, w, f"Chung-Lu n={n}, exponent 2.5, mean degree 8, seed 1, unit weights"
     raise KeyError(name)
