@@ -151,6 +151,37 @@ int cc_get_stats(cc_handle* h, cc_stats* st);
 /* Device bytes held by the handle. */
 int64_t cc_device_bytes(const cc_handle* h);
 
+/* Largest n that cc_check_noalloc accepts. */
+#define CC_NOALLOC_MAX_N 4096
+
+/* Convergence check without any allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * when they need the check, e.g. a program whose device memory is reserved
+ * in full by another allocator (a framework's pool, a plugin host with a
+ * fixed budget), or a latency-critical loop where cudaMalloc/cudaFree may
+ * synchronize the whole device.  It computes what cc_check reports, from the
+ * caller's own device arrays in the public layouts:
+ *   x, f, d, w   P = n(n-1)/2 doubles each, packed order (device pointers)
+ *   y_pair       2P doubles, packed order (device pointer)
+ *   out          8 doubles (device pointer, written): max_violation,
+ *                pair_violation, lp_objective, wf, qp_primal,
+ *                dual_objective, gap, 0
+ * and runs asynchronously on `stream` (cudaStream_t; NULL = legacy default
+ * stream) on the current device.  It calls no cudaMalloc/cudaFree and no
+ * allocating library routine.  Its scratch is a fixed array in the library's
+ * device memory of 6 * CC_NOALLOC_MAX_N doubles (192 KB), held on every GPU
+ * that loads the library until the process exits; n > CC_NOALLOC_MAX_N is
+ * rejected with CC_ERR_ARG.  The first call on a device looks up that
+ * array's device address (with the device current) and caches it; make that
+ * first call before any stream capture.  All calls share the one array, and
+ * each call writes every entry it later reads, so no clearing is needed;
+ * calls whose kernels overlap on the GPU (different streams, no ordering)
+ * race on it and must be serialized by the caller.  Errors: CC_ERR_ARG (NULL
+ * array, n < 3, n > CC_NOALLOC_MAX_N, eps <= 0), CC_ERR_CUDA; the message is
+ * in cc_last_error(NULL). */
+int cc_check_noalloc(int64_t n, double eps, const double* x, const double* f, const double* d,
+                     const double* w, const double* y_pair, double* out, void* stream);
+
 /* Release everything the handle owns.  NULL is a no-op. */
 void cc_destroy(cc_handle* h);
 

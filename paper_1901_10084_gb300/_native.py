@@ -69,7 +69,7 @@ class cc_stats(ctypes.Structure):
 
 EXPORTS = ("cc_opts_default", "cc_create", "cc_create_device", "cc_sweep", "cc_check",
            "cc_solve", "cc_get_x", "cc_get_duals", "cc_set_state", "cc_get_stats",
-           "cc_device_bytes", "cc_destroy", "cc_last_error")
+           "cc_device_bytes", "cc_destroy", "cc_last_error", "cc_check_noalloc")
 
 _lib = None
 _lock = threading.Lock()
@@ -121,6 +121,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         lib.cc_destroy.restype = None
         lib.cc_last_error.argtypes = [H]
         lib.cc_last_error.restype = ctypes.c_char_p
+        vp = ctypes.c_void_p
+        lib.cc_check_noalloc.argtypes = [i64, ctypes.c_double, vp, vp, vp, vp, vp, vp, vp]
+        lib.cc_check_noalloc.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -214,3 +217,13 @@ def cc_destroy(h) -> None:
 def cc_last_error(h=None) -> str:
     m = load().cc_last_error(h)
     return m.decode() if m else ""
+
+
+def cc_check_noalloc(n: int, eps: float, x_ptr: int, f_ptr: int, d_ptr: int, w_ptr: int,
+                     y_pair_ptr: int, out_ptr: int, stream: int = 0) -> int:
+    """Convergence check from caller-owned device arrays (packed layouts) into
+    a caller-owned device array of 8 doubles; allocates nothing.  Returns the
+    status code (CC_OK or an error; message in cc_last_error())."""
+    v = ctypes.c_void_p
+    return int(load().cc_check_noalloc(n, eps, v(x_ptr), v(f_ptr), v(d_ptr), v(w_ptr),
+                                       v(y_pair_ptr), v(out_ptr), v(stream)))

@@ -11,7 +11,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libccdyk.so")
-SOURCES = [os.path.join(CSRC, "ccdyk.cu")]
+SOURCES = [os.path.join(CSRC, "ccdyk.cu"), os.path.join(CSRC, "noalloc.cu")]
 DEPENDS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")] + [
     os.path.join(INCLUDE, "ccdyk.h")]
 

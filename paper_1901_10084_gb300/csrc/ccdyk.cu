@@ -368,6 +368,9 @@ int new_handle(cc_handle** out, int64_t n, const cc_opts* opts, cc_handle** hp) 
 
 }  // namespace
 
+// Message for cc_last_error(NULL) from entry points outside this file.
+void ccd_set_global_error(const char* msg) { g_create_error = msg ? msg : ""; }
+
 // ====================================================================== ABI
 
 extern "C" {
