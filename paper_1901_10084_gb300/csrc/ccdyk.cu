@@ -49,6 +49,9 @@ struct cc_handle {
   int* bt_off = nullptr;
   int* tile_list = nullptr;
   int* bt_rank = nullptr;
+  uint32_t* mask = nullptr;  // nonzero-dual bits (fused form)
+  int64_t mask_words = 0;
+  int* work = nullptr;       // per-phase work counters
   // scratch
   Ctl* ctl = nullptr;
   double* part = nullptr;    // reduction partials
@@ -136,11 +139,20 @@ void* sweep_kernel_b(int B) {
   }
 }
 
+template <typename T, bool UNITW>
+void* filtered_kernel_b(int B) {
+  switch (B) {
+    case 8: return (void*)k_sweep_filtered<T, UNITW, 8>;
+    case 16: return (void*)k_sweep_filtered<T, UNITW, 16>;
+    default: return (void*)k_sweep_filtered<T, UNITW, 32>;
+  }
+}
+
+// exact form: row-by-row kernel; fused form: filtered kernel
 void* sweep_kernel(cc_handle* h) {
-  const bool ex = h->o.exact != 0;
-  if (h->fp32) return h->unitw ? sweep_kernel_b<float, false, true>(h->B) : sweep_kernel_b<float, false, false>(h->B);
-  if (ex) return h->unitw ? sweep_kernel_b<double, true, true>(h->B) : sweep_kernel_b<double, true, false>(h->B);
-  return h->unitw ? sweep_kernel_b<double, false, true>(h->B) : sweep_kernel_b<double, false, false>(h->B);
+  if (h->o.exact) return h->unitw ? sweep_kernel_b<double, true, true>(h->B) : sweep_kernel_b<double, true, false>(h->B);
+  if (h->fp32) return h->unitw ? filtered_kernel_b<float, true>(h->B) : filtered_kernel_b<float, false>(h->B);
+  return h->unitw ? filtered_kernel_b<double, true>(h->B) : filtered_kernel_b<double, false>(h->B);
 }
 
 int threads_for_tile(int B) { return B * B < 256 ? B * B : 256; }
@@ -165,6 +177,8 @@ TiledArgs<T> tiled_args(cc_handle* h) {
   a.eps = (T)h->o.eps;
   a.r_unit = (T)(1.0 / 3.0);
   a.skip_cta = h->o.debug_skip_cta;
+  a.mask = h->mask;
+  a.work = h->work;
   return a;
 }
 
@@ -175,7 +189,10 @@ int configure_sweep(cc_handle* h) {
   CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0));
   if (per_sm < 1) return fail(h, CC_ERR_CUDA, "sweep kernel does not fit on an SM");
   int cap = per_sm * h->sms;
-  int g = h->o.grid > 0 ? std::min(h->o.grid, cap) : std::min(cap, std::max(1, h->max_bt_phase));
+  int g;
+  if (h->o.grid > 0) g = std::min(h->o.grid, cap);
+  else if (h->o.exact) g = std::min(cap, std::max(1, h->max_bt_phase));   // static: one item per CTA
+  else g = std::min(per_sm, 4) * h->sms;                                 // dynamic distribution
   h->sweep_grid = g;
   h->sweep_threads = threads;
   return CC_OK;
@@ -184,6 +201,7 @@ int configure_sweep(cc_handle* h) {
 int launch_sweep(cc_handle* h) {
   void* k = sweep_kernel(h);
   CK(h, cudaMemsetAsync(&h->ctl->arrive, 0, sizeof(unsigned), h->st));
+  if (h->work) CK(h, cudaMemsetAsync(h->work, 0, (size_t)h->nb * sizeof(int), h->st));
   if (h->fp32) {
     TiledArgs<float> a = tiled_args<float>(h);
     void* args[] = {&a};
@@ -201,15 +219,34 @@ int launch_sweep(cc_handle* h) {
 int build_tables(cc_handle* h) {
   const int nb = h->nb, B = h->B;
   std::vector<int> list, off(nb + 1, 0), rank((size_t)nb * nb * nb, -1), tiles;
+  // triplets in block triple (I,J,K): products of block sizes, with
+  // binomials where blocks coincide
+  auto bsize = [&](int I) { return (int64_t)std::min<int64_t>(B, h->n - (int64_t)I * B); };
+  auto count = [&](int I, int J, int K) -> int64_t {
+    if (I == J && J == K) return ch3(bsize(I));
+    if (I == J) return ch2(bsize(I)) * bsize(K);
+    if (J == K) return bsize(I) * ch2(bsize(J));
+    return bsize(I) * bsize(J) * bsize(K);
+  };
+  std::vector<std::pair<int64_t, int>> ph;
   for (int g = 0; g < nb; ++g) {
     off[g] = (int)list.size();
+    ph.clear();
     for (int I = 0; I < nb; ++I)
       for (int J = I; J < nb; ++J) {
         int K = ((g - I - J) % nb + 2 * nb) % nb;
         if (K < J) continue;
-        rank[((size_t)I * nb + J) * nb + K] = (int)list.size();
-        list.push_back(I | (J << 10) | (K << 20));
+        ph.push_back({-count(I, J, K), I | (J << 10) | (K << 20)});
       }
+    // largest first, so that the dynamic distribution ends the phase with
+    // the smallest items
+    std::stable_sort(ph.begin(), ph.end(),
+                     [](const std::pair<int64_t, int>& x, const std::pair<int64_t, int>& y) { return x.first < y.first; });
+    for (auto& e : ph) {
+      const int I = e.second & 1023, J = (e.second >> 10) & 1023, K = (e.second >> 20) & 1023;
+      rank[((size_t)I * nb + J) * nb + K] = (int)list.size();
+      list.push_back(e.second);
+    }
     h->max_bt_phase = std::max(h->max_bt_phase, (int)list.size() - off[g]);
   }
   off[nb] = (int)list.size();
@@ -299,6 +336,13 @@ int create_common(cc_handle** out, int64_t n, const double* d_dev, const double*
   h->zp = dalloc(h, te * 2 * h->esz);
   h->zt = dalloc(h, (size_t)h->zt_elems * h->esz);
   h->ctl = (Ctl*)dalloc(h, sizeof(Ctl));
+  if (!h->o.exact) {
+    h->mask_words = (int64_t)h->nbt * 3 * h->B * ((h->B * h->B) / 32);
+    h->mask = (uint32_t*)dalloc(h, (size_t)h->mask_words * sizeof(uint32_t));
+    h->work = (int*)dalloc(h, (size_t)h->nb * sizeof(int));
+    if (!h->mask || !h->work) return fail(h, CC_ERR_OOM, "dual bitmask");
+    CK(h, cudaMemsetAsync(h->mask, 0, (size_t)h->mask_words * sizeof(uint32_t), h->st));
+  }
   h->part_cap = std::max(8 * h->sms, 64);
   h->part = (double*)dalloc(h, (size_t)h->part_cap * 6 * sizeof(double));  // maxima, then 5 sums each
   if (!h->x || !h->f || !h->d || !h->winv || !h->zp || !h->zt || !h->ctl || !h->part)
@@ -628,6 +672,18 @@ int cc_set_state(cc_handle* h, const double* x, const double* f, const double* y
   CK(h, cudaStreamSynchronize(h->st));
   rc = move_duals(h, const_cast<double*>(y_tri), const_cast<double*>(y_pair), 0, h->T3, 1);
   if (rc) return rc;
+  if (h->mask) {
+    const int g2 = grid_for(h, h->mask_words, 256);
+#define LAUNCH_RM(T, BV) k_rebuild_mask<T, BV><<<g2, 256, 0, h->st>>>((const T*)h->zt, h->mask, h->mask_words);
+    if (h->fp32) {
+      if (h->B == 8) { LAUNCH_RM(float, 8) } else if (h->B == 16) { LAUNCH_RM(float, 16) } else { LAUNCH_RM(float, 32) }
+    } else {
+      if (h->B == 8) { LAUNCH_RM(double, 8) } else if (h->B == 16) { LAUNCH_RM(double, 16) } else { LAUNCH_RM(double, 32) }
+    }
+#undef LAUNCH_RM
+    CK(h, cudaGetLastError());
+    CK(h, cudaStreamSynchronize(h->st));
+  }
   h->sweeps = 0;
   return CC_OK;
 }

@@ -47,6 +47,8 @@ struct TiledArgs {
   T eps;                // eps of Eq. (qp)
   T r_unit;             // 1/3: 1/(a^T W^{-1} a) for unit weights
   int skip_cta;         // fault-injection hook (-1 = off)
+  uint32_t* mask;       // nonzero-dual bits, same schedule order as zt (filtered form)
+  int* work;            // per-phase work counters (dynamic distribution), zeroed per launch
 };
 
 __device__ __forceinline__ void unpack_bt(int pk, int& I, int& J, int& K) {
@@ -168,6 +170,208 @@ __global__ void __launch_bounds__(TileCfg<B>::NT) k_sweep_tiled(TiledArgs<T> a) 
   tiled_pair_phase<T, EXACT, B>(a);
 }
 
+// ------------------------------------------------------------ filtered sweep
+//
+// Most metric rows are inactive at any time: their dual is zero and the row
+// is satisfied (x_h - x_a - x_b <= 0), and then the fused update changes
+// nothing (z' = max(0 + r*delta, 0) = 0, c = 0).  The filtered sweep proves a
+// row inactive cheaply and skips it:
+//   * a bit per row records whether its dual is nonzero (same schedule order
+//     as the dual store; the store itself stays exact, zeros included), so
+//     zero duals are never read from HBM;
+//   * for FP64 state, a float copy of the x tiles in shared memory gives
+//     delta_f = (x_h - x_a) - x_b in float; with S = |x_h| + |x_a| + |x_b|
+//     (float), |delta_f - delta| <= 3.1 * 2^-24 * S (three conversions and two
+//     additions rounded to nearest), so delta_f <= -(2^-21 S + 2^-100)
+//     proves delta < 0 for the double evaluation as well;
+//   * for FP32 state the test is the fused form's own delta <= 0.
+// A triplet whose three rows are proved inactive is skipped; any other
+// triplet runs the fused form unchanged, so the result equals the unfiltered
+// sweep's in value.  Warps whose 32 triplets are all inactive skip the FP64
+// work entirely (a warp vote).
+
+__device__ __forceinline__ bool row_inactive_f(float h, float a, float b) {
+  const float dl = (h - a) - b;
+  const float S = fabsf(h) + fabsf(a) + fabsf(b);
+  return dl <= -fmaf(S, 0x1p-21f, 0x1p-100f);
+}
+
+template <typename T>
+__device__ __forceinline__ bool triplet_inactive(T xij, T xik, T xjk);
+
+template <>
+__device__ __forceinline__ bool triplet_inactive<float>(float xij, float xik, float xjk) {
+  return ((xij - xik) - xjk) <= 0.0f && ((xik - xij) - xjk) <= 0.0f && ((xjk - xij) - xik) <= 0.0f;
+}
+
+__device__ __forceinline__ bool triplet_inactive_shadow(float fij, float fik, float fjk) {
+  return row_inactive_f(fij, fik, fjk) && row_inactive_f(fik, fij, fjk) && row_inactive_f(fjk, fij, fik);
+}
+
+template <int B>
+struct MaskCfg {
+  static constexpr int WPR = (B * B) / 32;          // mask words per row and sub-phase
+  static constexpr int PER_BT = 3 * B * WPR;        // mask words per block triple
+};
+
+// Weights (rarely needed: only for triplets that are not skipped) are read
+// from L2 on demand instead of being staged.
+template <typename T, bool UNITW, int B>
+__device__ __forceinline__ void filtered_block_triple(const TiledArgs<T>& a, int w, T* s0, T* s1, T* s2,
+                                                      float* f0, float* f1, float* f2) {
+  using C = TileCfg<B>;
+  using M = MaskCfg<B>;
+  constexpr bool SHADOW = sizeof(T) == 8;
+  int I, J, K;
+  unpack_bt(a.bt_list[w], I, J, K);
+  const int64_t oIJ = tile_index(a.nb, I, J) * C::BB;
+  const int64_t oIK = tile_index(a.nb, I, K) * C::BB;
+  const int64_t oJK = tile_index(a.nb, J, K) * C::BB;
+  const bool kj = (K == J), ij = (I == J);
+  T* pIJ = s0;
+  T* pIK = kj ? s0 : s1;
+  T* pJK = ij ? pIK : s2;
+  float* gIJ = f0;
+  float* gIK = kj ? f0 : f1;
+  float* gJK = ij ? gIK : f2;
+  for (int e = threadIdx.x; e < C::BB; e += C::NT) {
+    const T v0 = ld_l2(a.x + oIJ + e);
+    s0[e] = v0;
+    if constexpr (SHADOW) f0[e] = (float)v0;
+    if (!kj) {
+      const T v1 = ld_l2(a.x + oIK + e);
+      s1[e] = v1;
+      if constexpr (SHADOW) f1[e] = (float)v1;
+    }
+    if (!ij) {
+      const T v2 = ld_l2(a.x + oJK + e);
+      s2[e] = v2;
+      if constexpr (SHADOW) f2[e] = (float)v2;
+    }
+  }
+  __syncthreads();
+  T* zb = a.zt + (int64_t)w * (3 * B * C::BB);
+  uint32_t* mb = a.mask + (int64_t)w * M::PER_BT;
+  const int kB = K * B;
+  const int lane = threadIdx.x & 31;
+  int touched = 0;
+  for (int t = 0; t < B; ++t) {
+    T* zs = zb + (int64_t)t * (3 * C::BB);
+    uint32_t* ms = mb + t * (3 * M::WPR);
+#pragma unroll
+    for (int q = 0; q < C::SPT; ++q) {
+      const int slot = threadIdx.x + q * C::NT;
+      const int la = slot / B, lb = slot % B;
+      const int lc = (t - la - lb) & (B - 1);
+      const bool valid = (!ij || la < lb) && (!kj || lb < lc) && (kB + lc < a.n);
+      const int wd = slot >> 5;
+      const uint32_t m0 = ms[wd], m1 = ms[M::WPR + wd], m2 = ms[2 * M::WPR + wd];
+      const bool b0 = (m0 >> lane) & 1u, b1 = (m1 >> lane) & 1u, b2 = (m2 >> lane) & 1u;
+      const int eij = la * B + lb, eik = la * B + lc, ejk = lb * B + lc;
+      bool need = false;
+      if (valid) {
+        if (b0 | b1 | b2) {
+          need = true;
+        } else {
+          if constexpr (SHADOW) need = !triplet_inactive_shadow(gIJ[eij], gIK[eik], gJK[ejk]);
+          else need = !triplet_inactive<T>(pIJ[eij], pIK[eik], pJK[ejk]);
+        }
+      }
+      if (__any_sync(0xffffffffu, need)) {
+        T z0 = T(0), z1 = T(0), z2 = T(0);
+        if (need) {
+          if (b0) z0 = ld_stream(zs + slot);
+          if (b1) z1 = ld_stream(zs + C::BB + slot);
+          if (b2) z2 = ld_stream(zs + 2 * C::BB + slot);
+          const T o0 = z0, o1 = z1, o2 = z2;
+          T xij = pIJ[eij], xik = pIK[eik], xjk = pJK[ejk];
+          T vij = T(1), vik = T(1), vjk = T(1);
+          if (!UNITW) {
+            vij = a.winv[oIJ + eij];
+            vik = a.winv[oIK + eik];
+            vjk = a.winv[oJK + ejk];
+          }
+          triplet_rows<T, false, UNITW>(xij, xik, xjk, vij, vik, vjk, a.eps, a.r_unit, z0, z1, z2);
+          pIJ[eij] = xij;
+          pIK[eik] = xik;
+          pJK[ejk] = xjk;
+          if constexpr (SHADOW) {
+            gIJ[eij] = (float)xij;
+            gIK[eik] = (float)xik;
+            gJK[ejk] = (float)xjk;
+          }
+          if (z0 != o0) st_stream(zs + slot, z0);
+          if (z1 != o1) st_stream(zs + C::BB + slot, z1);
+          if (z2 != o2) st_stream(zs + 2 * C::BB + slot, z2);
+          touched = 1;
+        }
+        const uint32_t n0 = __ballot_sync(0xffffffffu, need ? (z0 != T(0)) : b0);
+        const uint32_t n1 = __ballot_sync(0xffffffffu, need ? (z1 != T(0)) : b1);
+        const uint32_t n2 = __ballot_sync(0xffffffffu, need ? (z2 != T(0)) : b2);
+        if (lane == 0) {
+          if (n0 != m0) ms[wd] = n0;
+          if (n1 != m1) ms[M::WPR + wd] = n1;
+          if (n2 != m2) ms[2 * M::WPR + wd] = n2;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (__syncthreads_or(touched)) {
+    for (int e = threadIdx.x; e < C::BB; e += C::NT) {
+      a.x[oIJ + e] = s0[e];
+      if (!kj) a.x[oIK + e] = s1[e];
+      if (!ij) a.x[oJK + e] = s2[e];
+    }
+    __syncthreads();
+  }
+}
+
+// Dynamic distribution: CTAs take the block triples of a phase in list
+// order (largest first) from a per-phase counter.
+template <typename T, bool UNITW, int B>
+__global__ void __launch_bounds__(TileCfg<B>::NT) k_sweep_filtered(TiledArgs<T> a) {
+  using C = TileCfg<B>;
+  constexpr int NSH = sizeof(T) == 8 ? 3 : 1;
+  __shared__ T sx[3][C::BB];
+  __shared__ float sf[NSH][C::BB];
+  __shared__ int s_flag, s_item;
+  unsigned target = 0;
+  for (int g = 0; g < a.nb; ++g) {
+    const int beg = a.bt_off[g], cnt = a.bt_off[g + 1] - beg;
+    while (true) {
+      if (threadIdx.x == 0) s_item = atomicAdd(&a.work[g], 1);
+      __syncthreads();
+      const int k = s_item;
+      __syncthreads();
+      if (k >= cnt) break;
+      filtered_block_triple<T, UNITW, B>(a, beg + k, sx[0], sx[1], sx[2], sf[0], sf[NSH == 3 ? 1 : 0],
+                                         sf[NSH == 3 ? 2 : 0]);
+    }
+    target += gridDim.x;
+    const bool skip = (g == 0) && ((int)blockIdx.x == a.skip_cta);
+    if (!grid_barrier(a.ctl, target, a.timeout_ns, g, skip, &s_flag)) return;
+  }
+  tiled_pair_phase<T, false, B>(a);
+}
+
+// Rebuild the nonzero bits from the dual store (after the store was written
+// from outside a sweep).  One thread per mask word.
+template <typename T, int B>
+__global__ void k_rebuild_mask(const T* zt, uint32_t* mask, int64_t nwords) {
+  using M = MaskCfg<B>;
+  constexpr int BB = B * B;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nwords; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t w = q / M::PER_BT;
+    const int rem = (int)(q % M::PER_BT);
+    const int t = rem / (3 * M::WPR), r = (rem / M::WPR) % 3, wd = rem % M::WPR;
+    const T* z = zt + w * (3 * B * BB) + (int64_t)t * (3 * BB) + r * BB + wd * 32;
+    uint32_t bits = 0;
+    for (int l = 0; l < 32; ++l) bits |= (z[l] != T(0) ? 1u : 0u) << l;
+    mask[q] = bits;
+  }
+}
+
 // ------------------------------------------------------------ reductions
 
 template <typename V, typename Op>
@@ -194,24 +398,35 @@ struct SumOp {
 };
 
 // Largest metric-row violation max(0, x_h - x_a - x_b) over all triplets,
-// evaluated in FP64; one partial maximum per CTA.
+// evaluated in FP64; one partial maximum per CTA.  A row is evaluated in FP64
+// only when its float estimate can still exceed the running maximum m: with
+// S = |x_h| + |x_a| + |x_b| the float delta is within 3.1 * 2^-24 S of the
+// double one, and skipping rows with RN(delta_f + 2 tau) <= m_f (tau =
+// 2^-21 S + 2^-100, m_f = m rounded down to float) never skips a row above m.
+// The maximum is order-free, so the result equals a serial FP64 evaluation.
 template <typename T, int B>
 __global__ void __launch_bounds__(TileCfg<B>::NT) k_maxviol_tiled(const T* __restrict__ x, int n, int nb,
                                                                    const int* __restrict__ bt_list, int nbt,
                                                                    double* part) {
   using C = TileCfg<B>;
   __shared__ T sx[3][C::BB];
+  __shared__ float sf[3][C::BB];
   __shared__ double sred[32];
   double m = 0.0;
+  float mf = 0.0f;
   for (int w = blockIdx.x; w < nbt; w += gridDim.x) {
     int I, J, K;
     unpack_bt(bt_list[w], I, J, K);
     const int64_t oIJ = tile_index(nb, I, J) * C::BB, oIK = tile_index(nb, I, K) * C::BB,
                   oJK = tile_index(nb, J, K) * C::BB;
     for (int e = threadIdx.x; e < C::BB; e += C::NT) {
-      sx[0][e] = x[oIJ + e];
-      sx[1][e] = x[oIK + e];
-      sx[2][e] = x[oJK + e];
+      const T v0 = x[oIJ + e], v1 = x[oIK + e], v2 = x[oJK + e];
+      sx[0][e] = v0;
+      sx[1][e] = v1;
+      sx[2][e] = v2;
+      sf[0][e] = (float)v0;
+      sf[1][e] = (float)v1;
+      sf[2][e] = (float)v2;
     }
     __syncthreads();
     const bool kj = (K == J), ij = (I == J);
@@ -219,11 +434,22 @@ __global__ void __launch_bounds__(TileCfg<B>::NT) k_maxviol_tiled(const T* __res
     for (int slot = threadIdx.x; slot < C::BB; slot += C::NT) {
       const int la = slot / B, lb = slot % B;
       if (ij && la >= lb) continue;
-      const double xij = (double)sx[0][la * B + lb];
+      const float fij = sf[0][la * B + lb];
       for (int lc = kj ? lb + 1 : 0; lc < B && kB + lc < n; ++lc) {
-        const double xik = (double)sx[1][la * B + lc], xjk = (double)sx[2][lb * B + lc];
-        const double v0 = (xij - xik) - xjk, v1 = (xik - xij) - xjk, v2 = (xjk - xij) - xik;
-        m = fmax(m, fmax(v0, fmax(v1, v2)));
+        const float fik = sf[1][la * B + lc], fjk = sf[2][lb * B + lc];
+        const float S = fabsf(fij) + fabsf(fik) + fabsf(fjk);
+        const float tau2 = 2.0f * fmaf(S, 0x1p-21f, 0x1p-100f);
+        const float d0 = (fij - fik) - fjk, d1 = (fik - fij) - fjk, d2 = (fjk - fij) - fik;
+        if (d0 + tau2 > mf || d1 + tau2 > mf || d2 + tau2 > mf) {
+          const double xij = (double)sx[0][la * B + lb];
+          const double xik = (double)sx[1][la * B + lc], xjk = (double)sx[2][lb * B + lc];
+          const double v0 = (xij - xik) - xjk, v1 = (xik - xij) - xjk, v2 = (xjk - xij) - xik;
+          const double v = fmax(v0, fmax(v1, v2));
+          if (v > m) {
+            m = v;
+            mf = __double2float_rd(m);
+          }
+        }
       }
     }
     __syncthreads();

@@ -85,6 +85,38 @@ def test_fused_one_sweep_from_identical_state(n, tile, weighted, pre):
         _assert_state_close(_gpu_state(s), o, TOL_SWEEP)
 
 
+def _line_metric_state(n, seed, noise):
+    """x_ij = |p_i - p_j| for points on a line (every triplet has one row that
+    is tight up to rounding), plus noise of the given sizes on some pairs: rows
+    sit on both sides of zero, close to the float pre-filter's threshold."""
+    rng = np.random.default_rng(seed)
+    p = np.sort(rng.uniform(0, 1, n))
+    iu, ju = np.triu_indices(n, 1)
+    x = np.abs(p[iu] - p[ju])
+    sizes = rng.choice(noise, size=x.shape)
+    x = x + sizes * rng.choice([-1.0, 0.0, 1.0], size=x.shape)
+    return x
+
+
+@pytest.mark.parametrize("n,tile,weighted", [(40, 8, False), (70, 16, True), (90, 32, False)])
+def test_fused_near_tight_rows(n, tile, weighted):
+    """Rows with delta within a few float ulps of zero must not be skipped
+    wrongly: one fused sweep from such a state matches the oracle."""
+    d, w, _ = planted_partition(n, 3, 0.7, 0.2, seed=n, weights=(0.5, 2.0) if weighted else None)
+    o = oracle.State(n, d, w, 0.2)
+    o.x[:] = _line_metric_state(n, n, [1e-6, 1e-7, 1e-8, 1e-9, 1e-10, 0.0])
+    o.f[:] = 0.05
+    with _solver(n, d, w, eps=0.2, tile=tile) as s:
+        s.set_state(o.x, o.f, o.ytri, o.ypair)
+        st = s.check()
+        assert st["max_violation"] == o.max_violation()
+        s.sweep(1)
+        o.sweep(2, tile)
+        _assert_state_close(_gpu_state(s), o, TOL_SWEEP)
+        st = s.check()      # x now differs from the oracle's by rounding only
+        assert st["max_violation"] == pytest.approx(o.max_violation(), abs=1e-12)
+
+
 def test_fused_matches_over_many_sweeps_planted60():
     n, d, w, _ = workload("planted60")
     o = oracle.State(n, d, w, 0.2)
