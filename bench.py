@@ -42,6 +42,9 @@ def parse():
     p.add_argument("--tile", type=int, default=16)
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32_refine"])
     p.add_argument("--check-every", type=int, default=10)
+    p.add_argument("--variant", type=int, default=0)
+    p.add_argument("--schedule", default="tiled", choices=["tiled", "summod", "diagonal"])
+    p.add_argument("--grid", type=int, default=0)
     p.add_argument("--tol", type=float, default=1e-4)
     p.add_argument("--ttt-max-sweeps", type=int, default=3000)
     p.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance solve")
@@ -134,7 +137,8 @@ def run_ours(args, rank, world, local_rank):
     T = n * (n - 1) * (n - 2) // 6
     stream = torch.cuda.Stream()
     s = cc.Solver(n, d, w, eps=0.2, tile=args.tile, precision=args.precision,
-                  check_every=args.check_every, stream=stream)
+                  check_every=args.check_every, stream=stream, variant=args.variant, grid=args.grid,
+                  schedule=args.schedule)
     for _ in range(args.warmup):
         s.sweep(1)
     s.check()
@@ -182,7 +186,7 @@ def run_ours(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": desc, "n": n, "triplets": T, "eps": 0.2,
-                       "schedule": "tiled", "tile": args.tile, "precision": args.precision,
+                       "schedule": args.schedule, "tile": args.tile, "precision": args.precision,
                        "check_every": args.check_every,
                        "l2": "no flush: the dual store (%.2f GB) is larger than L2 and streams every "
                              "sweep; x (%.1f MB) stays L2-resident by design" % (

@@ -88,6 +88,9 @@ typedef struct cc_opts {
   int32_t debug_skip_cta;   /* test hook: this CTA skips its first barrier
                                arrival (-1 = off); the sweep then ends with
                                CC_ERR_TIMEOUT */
+  int32_t variant;          /* fused-form sweep kernel: 0 or 1 = one CTA per
+                               block triple (default), 2 = one warp per block
+                               triple (tile <= 16) */
 } cc_opts;
 
 typedef struct cc_stats {

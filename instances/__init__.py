@@ -97,6 +97,16 @@ def workload(name: str):
     if name == "chunglu3000w":
         d, w, _ = chung_lu(3000, 2.5, 10.0, seed=2, weights=(0.5, 2.0))
         return 3000, d, w, "Chung-Lu n=3000, exponent 2.5, mean degree 10, seed 2, w~U[0.5,2]"
+    if name == "chunglu1000perm":
+        n = 1000
+        d, w, _ = chung_lu(n, 2.5, 8.0, seed=1)
+        perm = np.random.default_rng(7).permutation(n)
+        D = np.zeros((n, n))
+        iu, ju = np.triu_indices(n, 1)
+        D[iu, ju] = d
+        D = D + D.T
+        Dp = D[np.ix_(perm, perm)]
+        return n, Dp[iu, ju].copy(), w, "Chung-Lu n=1000 as chunglu1000 with node labels permuted (seed 7)"
     if name.startswith("chunglu") and name[7:].isdigit():
         n = int(name[7:])
         d, w, _ = chung_lu(n, 2.5, 8.0, seed=1)

@@ -69,7 +69,7 @@ class Solver:
 
     def __init__(self, n, d, w, eps=0.2, schedule="tiled", tile=16, precision="fp64",
                  exact=False, check_every=10, device=0, stream=None, torch_alloc=True,
-                 barrier_timeout_s=2.0, grid=0, debug_skip_cta=-1, on_device=False):
+                 barrier_timeout_s=2.0, grid=0, debug_skip_cta=-1, on_device=False, variant=0):
         o = cc_opts_default()
         o.eps = float(eps)
         o.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
@@ -81,6 +81,7 @@ class Solver:
         o.barrier_timeout_s = float(barrier_timeout_s)
         o.grid = int(grid)
         o.debug_skip_cta = int(debug_skip_cta)
+        o.variant = int(variant)
         self._alloc = None
         try:
             import torch

@@ -47,6 +47,7 @@ class cc_opts(ctypes.Structure):
         ("alloc_ctx", ctypes.c_void_p),
         ("grid", ctypes.c_int32),
         ("debug_skip_cta", ctypes.c_int32),
+        ("variant", ctypes.c_int32),
     ]
 
 

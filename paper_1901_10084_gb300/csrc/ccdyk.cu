@@ -12,6 +12,7 @@
 #include "ccdyk.h"
 #include "common.cuh"
 #include "tiled.cuh"
+#include "listsched.cuh"
 
 using namespace ccd;
 
@@ -51,7 +52,16 @@ struct cc_handle {
   int* bt_rank = nullptr;
   uint32_t* mask = nullptr;  // nonzero-dual bits (fused form)
   int64_t mask_words = 0;
-  int* work = nullptr;       // per-phase work counters
+  int* flow = nullptr;       // dataflow sweep: item counter + visits per tile
+  // schedules 0 and 1 (device tables)
+  ListArgs la{};
+  int* l_pre1 = nullptr;
+  int64_t* l_phoff = nullptr;
+  int* l_sets = nullptr;
+  int64_t* l_setoff = nullptr;
+  int* l_setidx = nullptr;
+  int64_t max_units_phase = 0;
+  size_t dyn_smem = 0;       // dynamic shared memory of the sweep kernel
   // scratch
   Ctl* ctl = nullptr;
   double* part = nullptr;    // reduction partials
@@ -139,20 +149,46 @@ void* sweep_kernel_b(int B) {
   }
 }
 
+// warp-per-item kernel: warps per CTA
+int warps_per_cta(int B) { return B == 8 ? 8 : 4; }
+
+bool use_warp_kernel(const cc_handle* h) {
+  if (h->o.exact || h->B > 16) return false;
+  return h->o.variant == 2;
+}
+
 template <typename T, bool UNITW>
-void* filtered_kernel_b(int B) {
+void* filtered_kernel_b(int B, bool warp) {
+  if (warp) return B == 8 ? (void*)k_sweep_warpflow<T, UNITW, 8> : (void*)k_sweep_warpflow<T, UNITW, 16>;
   switch (B) {
-    case 8: return (void*)k_sweep_filtered<T, UNITW, 8>;
-    case 16: return (void*)k_sweep_filtered<T, UNITW, 16>;
-    default: return (void*)k_sweep_filtered<T, UNITW, 32>;
+    case 8: return (void*)k_sweep_flow<T, UNITW, 8>;
+    case 16: return (void*)k_sweep_flow<T, UNITW, 16>;
+    default: return (void*)k_sweep_flow<T, UNITW, 32>;
   }
 }
 
-// exact form: row-by-row kernel; fused form: filtered kernel
+size_t flow_smem(bool fp32, int B) {
+  if (fp32) return B == 8 ? sizeof(FlowSmem<float, 8>) : B == 16 ? sizeof(FlowSmem<float, 16>) : sizeof(FlowSmem<float, 32>);
+  return B == 8 ? sizeof(FlowSmem<double, 8>) : B == 16 ? sizeof(FlowSmem<double, 16>) : sizeof(FlowSmem<double, 32>);
+}
+
+template <typename T, bool EXACT, bool UNITW>
+void* list_kernel(int sched) {
+  return sched == CC_SCHED_SUMMOD ? (void*)k_sweep_summod<T, EXACT, UNITW> : (void*)k_sweep_diagonal<T, EXACT, UNITW>;
+}
+
+// exact form: row-by-row kernel with grid barriers; fused form: filtered dataflow kernel
 void* sweep_kernel(cc_handle* h) {
+  if (h->o.schedule != CC_SCHED_TILED) {
+    const int sc = h->o.schedule;
+    if (h->o.exact) return h->unitw ? list_kernel<double, true, true>(sc) : list_kernel<double, true, false>(sc);
+    if (h->fp32) return h->unitw ? list_kernel<float, false, true>(sc) : list_kernel<float, false, false>(sc);
+    return h->unitw ? list_kernel<double, false, true>(sc) : list_kernel<double, false, false>(sc);
+  }
   if (h->o.exact) return h->unitw ? sweep_kernel_b<double, true, true>(h->B) : sweep_kernel_b<double, true, false>(h->B);
-  if (h->fp32) return h->unitw ? filtered_kernel_b<float, true>(h->B) : filtered_kernel_b<float, false>(h->B);
-  return h->unitw ? filtered_kernel_b<double, true>(h->B) : filtered_kernel_b<double, false>(h->B);
+  const bool wk = use_warp_kernel(h);
+  if (h->fp32) return h->unitw ? filtered_kernel_b<float, true>(h->B, wk) : filtered_kernel_b<float, false>(h->B, wk);
+  return h->unitw ? filtered_kernel_b<double, true>(h->B, wk) : filtered_kernel_b<double, false>(h->B, wk);
 }
 
 int threads_for_tile(int B) { return B * B < 256 ? B * B : 256; }
@@ -178,21 +214,37 @@ TiledArgs<T> tiled_args(cc_handle* h) {
   a.r_unit = (T)(1.0 / 3.0);
   a.skip_cta = h->o.debug_skip_cta;
   a.mask = h->mask;
-  a.work = h->work;
+  a.work = nullptr;
+  a.nbt = h->nbt;
   return a;
 }
 
 int configure_sweep(cc_handle* h) {
   void* k = sweep_kernel(h);
-  const int threads = threads_for_tile(h->B);
+  if (h->o.schedule != CC_SCHED_TILED) {
+    int per_sm = 0;
+    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, 0));
+    if (per_sm < 1) return fail(h, CC_ERR_CUDA, "sweep kernel does not fit on an SM");
+    const int64_t need = std::max<int64_t>(1, (std::max<int64_t>(h->max_units_phase, h->tile_elems / 4) + 255) / 256);
+    int g = (int)std::min<int64_t>((int64_t)per_sm * h->sms, need);
+    if (h->o.grid > 0) g = std::min(h->o.grid, per_sm * h->sms);
+    h->sweep_grid = g;
+    h->sweep_threads = 256;
+    h->dyn_smem = 0;
+    return CC_OK;
+  }
+  const bool wk = use_warp_kernel(h);
+  const int threads = wk ? 32 * warps_per_cta(h->B) : threads_for_tile(h->B);
+  h->dyn_smem = h->o.exact ? 0 : flow_smem(h->fp32, h->B) * (wk ? warps_per_cta(h->B) : 1);
+  if (h->dyn_smem) CK(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->dyn_smem));
   int per_sm = 0;
-  CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0));
+  CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, h->dyn_smem));
   if (per_sm < 1) return fail(h, CC_ERR_CUDA, "sweep kernel does not fit on an SM");
   int cap = per_sm * h->sms;
   int g;
   if (h->o.grid > 0) g = std::min(h->o.grid, cap);
   else if (h->o.exact) g = std::min(cap, std::max(1, h->max_bt_phase));   // static: one item per CTA
-  else g = std::min(per_sm, 4) * h->sms;                                 // dynamic distribution
+  else g = std::min(per_sm, 8) * h->sms;                                 // dataflow: all resident
   h->sweep_grid = g;
   h->sweep_threads = threads;
   return CC_OK;
@@ -200,16 +252,37 @@ int configure_sweep(cc_handle* h) {
 
 int launch_sweep(cc_handle* h) {
   void* k = sweep_kernel(h);
-  CK(h, cudaMemsetAsync(&h->ctl->arrive, 0, sizeof(unsigned), h->st));
-  if (h->work) CK(h, cudaMemsetAsync(h->work, 0, (size_t)h->nb * sizeof(int), h->st));
-  if (h->fp32) {
-    TiledArgs<float> a = tiled_args<float>(h);
-    void* args[] = {&a};
-    CK(h, cudaLaunchCooperativeKernel(k, h->sweep_grid, h->sweep_threads, args, 0, h->st));
-  } else {
+  if (h->o.schedule != CC_SCHED_TILED) {
+    CK(h, cudaMemsetAsync(&h->ctl->arrive, 0, sizeof(unsigned), h->st));
+    ListArgs L = h->la;
+    if (h->fp32) {
+      TiledArgs<float> a = tiled_args<float>(h);
+      void* args[] = {&a, &L};
+      CK(h, cudaLaunchCooperativeKernel(k, h->sweep_grid, h->sweep_threads, args, 0, h->st));
+    } else {
+      TiledArgs<double> a = tiled_args<double>(h);
+      void* args[] = {&a, &L};
+      CK(h, cudaLaunchCooperativeKernel(k, h->sweep_grid, h->sweep_threads, args, 0, h->st));
+    }
+    return CC_OK;
+  }
+  if (h->o.exact) {
+    CK(h, cudaMemsetAsync(&h->ctl->arrive, 0, sizeof(unsigned), h->st));
     TiledArgs<double> a = tiled_args<double>(h);
     void* args[] = {&a};
     CK(h, cudaLaunchCooperativeKernel(k, h->sweep_grid, h->sweep_threads, args, 0, h->st));
+    return CC_OK;
+  }
+  CK(h, cudaMemsetAsync(h->flow, 0, (size_t)(1 + h->ntiles) * sizeof(int), h->st));
+  int* flow = h->flow;
+  if (h->fp32) {
+    TiledArgs<float> a = tiled_args<float>(h);
+    void* args[] = {&a, &flow};
+    CK(h, cudaLaunchCooperativeKernel(k, h->sweep_grid, h->sweep_threads, args, h->dyn_smem, h->st));
+  } else {
+    TiledArgs<double> a = tiled_args<double>(h);
+    void* args[] = {&a, &flow};
+    CK(h, cudaLaunchCooperativeKernel(k, h->sweep_grid, h->sweep_threads, args, h->dyn_smem, h->st));
   }
   return CC_OK;
 }
@@ -266,6 +339,79 @@ int build_tables(cc_handle* h) {
   CK(h, cudaMemcpyAsync(h->bt_rank, rank.data(), rank.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
   CK(h, cudaMemcpyAsync(h->tile_list, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
   CK(h, cudaStreamSynchronize(h->st));  // host vectors go out of scope
+  return CC_OK;
+}
+
+// Tables of schedules 0 and 1 (O(n^2) integers; no triplet lists).
+int build_list_tables(cc_handle* h) {
+  const int n = (int)h->n;
+  ListArgs& L = h->la;
+  L.sched = h->o.schedule;
+  L.B = h->B;
+  if (L.sched == CC_SCHED_SUMMOD) {
+    L.nphases = n;
+    std::vector<int> pre1((size_t)n * (n + 1));
+    std::vector<int64_t> phoff(n + 1, 0);
+    for (int s = 0; s < n; ++s) {
+      int run = 0;
+      for (int i = 0; i < n; ++i) {
+        pre1[(size_t)s * (n + 1) + i] = run;
+        for (int q = 0; q < 3; ++q) {
+          const int m = s + q * n;
+          const int jlo = std::max(i + 1, m - i - n + 1);
+          const int jhi = (m - i - 1) >= 0 ? (m - i - 1) / 2 : -1;
+          if (jhi >= jlo) run += jhi - jlo + 1;
+        }
+      }
+      pre1[(size_t)s * (n + 1) + n] = run;
+      phoff[s + 1] = phoff[s] + run;
+      h->max_units_phase = std::max<int64_t>(h->max_units_phase, run);
+    }
+    if (phoff[n] != h->T3) return fail(h, CC_ERR_ARG, "schedule 1 table does not cover every triplet");
+    h->l_pre1 = (int*)dalloc(h, pre1.size() * sizeof(int));
+    h->l_phoff = (int64_t*)dalloc(h, phoff.size() * sizeof(int64_t));
+    if (!h->l_pre1 || !h->l_phoff) return fail(h, CC_ERR_OOM, "schedule tables");
+    CK(h, cudaMemcpyAsync(h->l_pre1, pre1.data(), pre1.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
+    CK(h, cudaMemcpyAsync(h->l_phoff, phoff.data(), phoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+  } else {
+    // the listing of the sets S_{i,k} (1-based x, z, c as printed; stored 0-based)
+    std::vector<int> sets, setidx((size_t)n * n, -1);
+    std::vector<int64_t> setoff, phoff;
+    int64_t run = 0;
+    auto add_phase = [&](int x, int z) {
+      phoff.push_back((int64_t)sets.size());
+      const int g = (z - x - 2) / 2;
+      for (int c = 0; c <= g; ++c) {
+        const int i = x + c - 1, k = z - c - 1;
+        setidx[(size_t)i * n + k] = (int)sets.size();
+        sets.push_back(i | (k << 16));
+        setoff.push_back(run);
+        run += k - i - 1;
+      }
+      h->max_units_phase = std::max<int64_t>(h->max_units_phase, g + 1);
+    };
+    for (int z = n; z >= 3; --z) add_phase(1, z);
+    for (int x = 2; x <= n - 2; ++x) add_phase(x, n);
+    L.nphases = (int)phoff.size();
+    phoff.push_back((int64_t)sets.size());
+    if (run != h->T3) return fail(h, CC_ERR_ARG, "schedule 0 table does not cover every triplet");
+    h->l_sets = (int*)dalloc(h, sets.size() * sizeof(int));
+    h->l_setoff = (int64_t*)dalloc(h, setoff.size() * sizeof(int64_t));
+    h->l_phoff = (int64_t*)dalloc(h, phoff.size() * sizeof(int64_t));
+    h->l_setidx = (int*)dalloc(h, setidx.size() * sizeof(int));
+    if (!h->l_sets || !h->l_setoff || !h->l_phoff || !h->l_setidx) return fail(h, CC_ERR_OOM, "schedule tables");
+    CK(h, cudaMemcpyAsync(h->l_sets, sets.data(), sets.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
+    CK(h, cudaMemcpyAsync(h->l_setoff, setoff.data(), setoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h->st));
+    CK(h, cudaMemcpyAsync(h->l_phoff, phoff.data(), phoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h->st));
+    CK(h, cudaMemcpyAsync(h->l_setidx, setidx.data(), setidx.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+  }
+  L.pre1 = h->l_pre1;
+  L.phoff = h->l_phoff;
+  L.sets = h->l_sets;
+  L.setoff = h->l_setoff;
+  L.setidx = h->l_setidx;
   return CC_OK;
 }
 
@@ -326,6 +472,11 @@ int create_common(cc_handle** out, int64_t n, const double* d_dev, const double*
   h->unitw = hf[2] == 0;
   int rc = build_tables(h);
   if (rc) return rc;
+  if (h->o.schedule != CC_SCHED_TILED) {
+    rc = build_list_tables(h);
+    if (rc) return rc;
+    h->zt_elems = 3 * h->T3;   // compact store in schedule order
+  }
   h->fp32 = h->o.precision == CC_PREC_FP32_REFINE;
   h->esz = h->fp32 ? 4 : 8;
   const size_t te = (size_t)h->tile_elems;
@@ -336,11 +487,11 @@ int create_common(cc_handle** out, int64_t n, const double* d_dev, const double*
   h->zp = dalloc(h, te * 2 * h->esz);
   h->zt = dalloc(h, (size_t)h->zt_elems * h->esz);
   h->ctl = (Ctl*)dalloc(h, sizeof(Ctl));
-  if (!h->o.exact) {
+  if (!h->o.exact && h->o.schedule == CC_SCHED_TILED) {
     h->mask_words = (int64_t)h->nbt * 3 * h->B * ((h->B * h->B) / 32);
     h->mask = (uint32_t*)dalloc(h, (size_t)h->mask_words * sizeof(uint32_t));
-    h->work = (int*)dalloc(h, (size_t)h->nb * sizeof(int));
-    if (!h->mask || !h->work) return fail(h, CC_ERR_OOM, "dual bitmask");
+    h->flow = (int*)dalloc(h, (size_t)(1 + h->ntiles) * sizeof(int));
+    if (!h->mask || !h->flow) return fail(h, CC_ERR_OOM, "dual bitmask");
     CK(h, cudaMemsetAsync(h->mask, 0, (size_t)h->mask_words * sizeof(uint32_t), h->st));
   }
   h->part_cap = std::max(8 * h->sms, 64);
@@ -374,8 +525,8 @@ int create_common(cc_handle** out, int64_t n, const double* d_dev, const double*
 int check_opts(const cc_opts& o) {
   if (!(o.eps > 0.0) || !std::isfinite(o.eps)) return fail(nullptr, CC_ERR_ARG, "eps must be finite and > 0");
   if (o.tile != 8 && o.tile != 16 && o.tile != 32) return fail(nullptr, CC_ERR_ARG, "tile must be 8, 16 or 32");
-  if (o.schedule != CC_SCHED_TILED)
-    return fail(nullptr, CC_ERR_UNSUPPORTED, "only the tiled schedule is served by this build");
+  if (o.schedule != CC_SCHED_TILED && o.schedule != CC_SCHED_SUMMOD && o.schedule != CC_SCHED_DIAGONAL)
+    return fail(nullptr, CC_ERR_ARG, "unknown schedule");
   if (o.precision != CC_PREC_FP64 && o.precision != CC_PREC_FP32_REFINE)
     return fail(nullptr, CC_ERR_ARG, "unknown precision");
   if (o.exact && o.precision != CC_PREC_FP64) return fail(nullptr, CC_ERR_ARG, "exact mode needs FP64");
@@ -611,6 +762,17 @@ static int move_duals(cc_handle* h, double* y_tri, double* y_pair, int64_t first
       if (dir == 1)
         CK(h, cudaMemcpyAsync(h->stage, y_tri + 3 * c0, 3 * m * sizeof(double), cudaMemcpyHostToDevice, h->st));
       const int g = grid_for(h, m, 256);
+      if (h->o.schedule != CC_SCHED_TILED) {
+        if (h->fp32)
+          k_tri_duals_list<float><<<g, 256, 0, h->st>>>((float*)h->zt, h->la, (int)h->n, first + c0, m, h->stage, scale, dir);
+        else
+          k_tri_duals_list<double><<<g, 256, 0, h->st>>>((double*)h->zt, h->la, (int)h->n, first + c0, m, h->stage, scale, dir);
+        CK(h, cudaGetLastError());
+        if (dir == 0)
+          CK(h, cudaMemcpyAsync(y_tri + 3 * c0, h->stage, 3 * m * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        CK(h, cudaStreamSynchronize(h->st));
+        continue;
+      }
 #define LAUNCH_TD(T, BV) \
   k_tri_duals_tiled<T, BV><<<g, 256, 0, h->st>>>((T*)h->zt, h->bt_rank, (int)h->n, h->nb, first + c0, m, h->stage, scale, dir);
       if (h->fp32) {

@@ -48,7 +48,8 @@ struct TiledArgs {
   T r_unit;             // 1/3: 1/(a^T W^{-1} a) for unit weights
   int skip_cta;         // fault-injection hook (-1 = off)
   uint32_t* mask;       // nonzero-dual bits, same schedule order as zt (filtered form)
-  int* work;            // per-phase work counters (dynamic distribution), zeroed per launch
+  int* work;            // unused
+  int nbt;              // block triples per sweep
 };
 
 __device__ __forceinline__ void unpack_bt(int pk, int& I, int& J, int& K) {
@@ -212,60 +213,182 @@ template <int B>
 struct MaskCfg {
   static constexpr int WPR = (B * B) / 32;          // mask words per row and sub-phase
   static constexpr int PER_BT = 3 * B * WPR;        // mask words per block triple
+  static constexpr int CAP = 2 * B * B;             // nonzero duals staged per block triple
 };
 
-// Weights (rarely needed: only for triplets that are not skipped) are read
-// from L2 on demand instead of being staged.
-template <typename T, bool UNITW, int B>
-__device__ __forceinline__ void filtered_block_triple(const TiledArgs<T>& a, int w, T* s0, T* s1, T* s2,
-                                                      float* f0, float* f1, float* f2) {
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_ca(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ int ld_acquire_s32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Shared-memory layout of one CTA of the dataflow sweep (dynamic shared memory).
+template <typename T, int B>
+struct alignas(16) FlowSmem {
+  static constexpr int BB = B * B;
+  static constexpr int NSH = sizeof(T) == 8 ? 3 : 1;
+  T x[3][BB];
+  float f[NSH][BB];
+  uint32_t mask[MaskCfg<B>::PER_BT];
+  int pre[MaskCfg<B>::PER_BT];
+  T dual[MaskCfg<B>::CAP];
+  int scan[32];
+  int item, flag, total;
+};
+
+// Wait (thread 0) until each listed tile has been visited `need` times.
+// Bounded in time; on expiry records CC_ERR_TIMEOUT.  Returns false when the
+// kernel must stop.
+__device__ __forceinline__ bool wait_tiles(const int* cnt, int64_t t0, int64_t t1, int64_t t2, int need,
+                                           Ctl* ctl, long long timeout_ns, int tag) {
+  const int64_t ts[3] = {t0, t1, t2};
+  unsigned long long start = 0;
+  unsigned spins = 0;
+  for (int q = 0; q < 3; ++q) {
+    if (ts[q] < 0) continue;
+    while (ld_acquire_s32(cnt + ts[q]) < need) {
+      if (ld_relaxed_s32(&ctl->err) != 0) return false;
+      if (start == 0) start = global_ns();
+      if ((++spins & 15u) == 0 && (long long)(global_ns() - start) > timeout_ns) {
+        if (atomicCAS(&ctl->err, 0, CC_ERR_TIMEOUT) == 0) ctl->err_phase = tag;
+        return false;
+      }
+      __nanosleep(128);
+    }
+  }
+  return true;
+}
+
+template <bool WARP>
+__device__ __forceinline__ void item_sync() {
+  if constexpr (WARP) __syncwarp();
+  else __syncthreads();
+}
+
+// One block triple, processed by one CTA (WARP = false) or by one warp alone
+// (WARP = true): stage tiles, mask and nonzero duals in shared memory
+// (asynchronous copies, one round of memory latency per item), then walk
+// the B sub-phases.
+template <typename T, bool UNITW, int B, bool WARP>
+__device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, int I, int J, int K,
+                                                  FlowSmem<T, B>& sm) {
   using C = TileCfg<B>;
   using M = MaskCfg<B>;
   constexpr bool SHADOW = sizeof(T) == 8;
-  int I, J, K;
-  unpack_bt(a.bt_list[w], I, J, K);
+  constexpr int NTH = WARP ? 32 : C::NT;         // threads working on the item
+  constexpr int SPT = C::BB / NTH;               // slots per thread and sub-phase
+  constexpr int NW = NTH / 32;
+  const int tid = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int64_t oIJ = tile_index(a.nb, I, J) * C::BB;
   const int64_t oIK = tile_index(a.nb, I, K) * C::BB;
   const int64_t oJK = tile_index(a.nb, J, K) * C::BB;
   const bool kj = (K == J), ij = (I == J);
-  T* pIJ = s0;
-  T* pIK = kj ? s0 : s1;
-  T* pJK = ij ? pIK : s2;
-  float* gIJ = f0;
-  float* gIK = kj ? f0 : f1;
-  float* gJK = ij ? gIK : f2;
-  for (int e = threadIdx.x; e < C::BB; e += C::NT) {
-    const T v0 = ld_l2(a.x + oIJ + e);
-    s0[e] = v0;
-    if constexpr (SHADOW) f0[e] = (float)v0;
-    if (!kj) {
-      const T v1 = ld_l2(a.x + oIK + e);
-      s1[e] = v1;
-      if constexpr (SHADOW) f1[e] = (float)v1;
+  T* pIJ = sm.x[0];
+  T* pIK = kj ? sm.x[0] : sm.x[1];
+  T* pJK = ij ? pIK : sm.x[2];
+  float* gIJ = sm.f[0];
+  float* gIK = SHADOW ? (kj ? sm.f[0] : sm.f[SHADOW ? 1 : 0]) : sm.f[0];
+  float* gJK = SHADOW ? (ij ? gIK : sm.f[SHADOW ? 2 : 0]) : sm.f[0];
+  T* zb = a.zt + (int64_t)w * (3 * B * C::BB);
+  const uint32_t* mb = a.mask + (int64_t)w * M::PER_BT;
+
+  // round 1: x tiles and mask words (16-byte copies, L2 only)
+  constexpr int XCH = C::BB * (int)sizeof(T) / 16;     // 16-byte chunks per tile
+  for (int e = tid; e < XCH; e += NTH) {
+    cp_async16(reinterpret_cast<char*>(sm.x[0]) + 16 * e, reinterpret_cast<const char*>(a.x + oIJ) + 16 * e);
+    if (!kj) cp_async16(reinterpret_cast<char*>(sm.x[1]) + 16 * e, reinterpret_cast<const char*>(a.x + oIK) + 16 * e);
+    if (!ij) cp_async16(reinterpret_cast<char*>(sm.x[2]) + 16 * e, reinterpret_cast<const char*>(a.x + oJK) + 16 * e);
+  }
+  constexpr int MCH = M::PER_BT * 4 / 16;
+  for (int e = tid; e < MCH; e += NTH)
+    cp_async16(reinterpret_cast<char*>(sm.mask) + 16 * e, reinterpret_cast<const char*>(mb) + 16 * e);
+  cp_async_wait_all();
+  item_sync<WARP>();
+
+  // exclusive prefix of the mask popcounts (the staging slot of each nonzero dual)
+  constexpr int CH = (M::PER_BT + NTH - 1) / NTH;
+  int cnt = 0;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int q = tid * CH + c;
+    if (q < M::PER_BT) cnt += __popc(sm.mask[q]);
+  }
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) sm.scan[wid] = incl;
+  item_sync<WARP>();
+  if (wid == 0) {
+    int v = lane < NW ? sm.scan[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
     }
-    if (!ij) {
-      const T v2 = ld_l2(a.x + oJK + e);
-      s2[e] = v2;
-      if constexpr (SHADOW) f2[e] = (float)v2;
+    if (lane < NW) sm.scan[lane] = v;
+  }
+  item_sync<WARP>();
+  int run = (wid ? sm.scan[wid - 1] : 0) + incl - cnt;
+  const int total = sm.scan[NW - 1];
+  const bool staged = total <= M::CAP;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int q = tid * CH + c;
+    if (q < M::PER_BT) {
+      uint32_t bits = sm.mask[q];
+      sm.pre[q] = run;
+      if (staged && bits) {
+        const int t = q / (3 * M::WPR), r = (q / M::WPR) % 3, wd = q % M::WPR;
+        const T* src = zb + (int64_t)t * (3 * C::BB) + r * C::BB + wd * 32;
+        int idx = run;
+        while (bits) {
+          const int l = __ffs(bits) - 1;
+          bits &= bits - 1;
+          cp_async_ca<sizeof(T)>(&sm.dual[idx++], src + l);
+        }
+      }
+      run += __popc(sm.mask[q]);
     }
   }
-  __syncthreads();
-  T* zb = a.zt + (int64_t)w * (3 * B * C::BB);
-  uint32_t* mb = a.mask + (int64_t)w * M::PER_BT;
+  if constexpr (SHADOW) {
+    for (int e = tid; e < C::BB; e += NTH) {
+      sm.f[0][e] = (float)sm.x[0][e];
+      if (!kj) sm.f[SHADOW ? 1 : 0][e] = (float)sm.x[1][e];
+      if (!ij) sm.f[SHADOW ? 2 : 0][e] = (float)sm.x[2][e];
+    }
+  }
+  cp_async_wait_all();
+  item_sync<WARP>();
+
   const int kB = K * B;
-  const int lane = threadIdx.x & 31;
   int touched = 0;
   for (int t = 0; t < B; ++t) {
     T* zs = zb + (int64_t)t * (3 * C::BB);
-    uint32_t* ms = mb + t * (3 * M::WPR);
-#pragma unroll
-    for (int q = 0; q < C::SPT; ++q) {
-      const int slot = threadIdx.x + q * C::NT;
+    const int qt = t * (3 * M::WPR);
+    for (int q = 0; q < SPT; ++q) {
+      const int slot = tid + q * NTH;
       const int la = slot / B, lb = slot % B;
       const int lc = (t - la - lb) & (B - 1);
       const bool valid = (!ij || la < lb) && (!kj || lb < lc) && (kB + lc < a.n);
       const int wd = slot >> 5;
-      const uint32_t m0 = ms[wd], m1 = ms[M::WPR + wd], m2 = ms[2 * M::WPR + wd];
+      const int q0 = qt + wd, q1 = qt + M::WPR + wd, q2 = qt + 2 * M::WPR + wd;
+      const uint32_t m0 = sm.mask[q0], m1 = sm.mask[q1], m2 = sm.mask[q2];
+      const uint32_t below = (1u << lane) - 1u;
       const bool b0 = (m0 >> lane) & 1u, b1 = (m1 >> lane) & 1u, b2 = (m2 >> lane) & 1u;
       const int eij = la * B + lb, eik = la * B + lc, ejk = lb * B + lc;
       bool need = false;
@@ -280,9 +403,15 @@ __device__ __forceinline__ void filtered_block_triple(const TiledArgs<T>& a, int
       if (__any_sync(0xffffffffu, need)) {
         T z0 = T(0), z1 = T(0), z2 = T(0);
         if (need) {
-          if (b0) z0 = ld_stream(zs + slot);
-          if (b1) z1 = ld_stream(zs + C::BB + slot);
-          if (b2) z2 = ld_stream(zs + 2 * C::BB + slot);
+          if (staged) {
+            if (b0) z0 = sm.dual[sm.pre[q0] + __popc(m0 & below)];
+            if (b1) z1 = sm.dual[sm.pre[q1] + __popc(m1 & below)];
+            if (b2) z2 = sm.dual[sm.pre[q2] + __popc(m2 & below)];
+          } else {
+            if (b0) z0 = ld_stream(zs + slot);
+            if (b1) z1 = ld_stream(zs + C::BB + slot);
+            if (b2) z2 = ld_stream(zs + 2 * C::BB + slot);
+          }
           const T o0 = z0, o1 = z1, o2 = z2;
           T xij = pIJ[eij], xik = pIK[eik], xjk = pJK[ejk];
           T vij = T(1), vik = T(1), vjk = T(1);
@@ -309,50 +438,147 @@ __device__ __forceinline__ void filtered_block_triple(const TiledArgs<T>& a, int
         const uint32_t n1 = __ballot_sync(0xffffffffu, need ? (z1 != T(0)) : b1);
         const uint32_t n2 = __ballot_sync(0xffffffffu, need ? (z2 != T(0)) : b2);
         if (lane == 0) {
-          if (n0 != m0) ms[wd] = n0;
-          if (n1 != m1) ms[M::WPR + wd] = n1;
-          if (n2 != m2) ms[2 * M::WPR + wd] = n2;
+          uint32_t* mw = a.mask + (int64_t)w * M::PER_BT;
+          if (n0 != m0) mw[q0] = n0;
+          if (n1 != m1) mw[q1] = n1;
+          if (n2 != m2) mw[q2] = n2;
         }
       }
     }
-    __syncthreads();
+    item_sync<WARP>();
   }
-  if (__syncthreads_or(touched)) {
-    for (int e = threadIdx.x; e < C::BB; e += C::NT) {
-      a.x[oIJ + e] = s0[e];
-      if (!kj) a.x[oIK + e] = s1[e];
-      if (!ij) a.x[oJK + e] = s2[e];
+  bool any_touched;
+  if constexpr (WARP) any_touched = __any_sync(0xffffffffu, touched);
+  else any_touched = __syncthreads_or(touched);
+  if (any_touched) {
+    for (int e = tid; e < C::BB; e += NTH) {
+      a.x[oIJ + e] = sm.x[0][e];
+      if (!kj) a.x[oIK + e] = sm.x[1][e];
+      if (!ij) a.x[oJK + e] = sm.x[2][e];
     }
-    __syncthreads();
+  }
+  item_sync<WARP>();
+}
+
+// The pair rows of one tile (a pair item of the dataflow sweep).
+template <typename T, int B, bool WARP>
+__device__ __forceinline__ void flow_pair_tile(const TiledArgs<T>& a, int tl) {
+  using C = TileCfg<B>;
+  constexpr int NTH = WARP ? 32 : C::NT;
+  const int tid = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+  const int pk = a.tile_list[tl];
+  const int I = pk & 0xffff, J = pk >> 16;
+  for (int slot = tid; slot < C::BB; slot += NTH) {
+    const int la = slot / B, lb = slot % B;
+    if ((I < J || la < lb) && J * B + lb < a.n) {
+      const int64_t e = (int64_t)tl * C::BB + slot;
+      T* zq = a.zp + (int64_t)tl * (2 * C::BB) + slot;
+      T x = ld_l2(a.x + e), f = a.f[e];
+      T zp = zq[0], zm = zq[C::BB];
+      pair_rows<T, false>(x, f, a.d[e], a.winv[e], a.eps, zp, zm);
+      a.x[e] = x;
+      a.f[e] = f;
+      zq[0] = zp;
+      zq[C::BB] = zm;
+    }
   }
 }
 
-// Dynamic distribution: CTAs take the block triples of a phase in list
-// order (largest first) from a per-phase counter.
+// One sweep as a dataflow over tiles.  Work items, taken in order from one
+// counter: the block triples in schedule order (phase-major, largest first
+// inside a phase), then one pair item per tile.  Every phase visits every
+// tile exactly once, so a block triple of phase g may start once each of its
+// tiles has g visits (counters in `tile_cnt`), and a tile's pair item once it
+// has Nb.  No grid-wide barrier: a CTA waits only for the items it depends
+// on, which were taken earlier by resident CTAs.
 template <typename T, bool UNITW, int B>
-__global__ void __launch_bounds__(TileCfg<B>::NT) k_sweep_filtered(TiledArgs<T> a) {
-  using C = TileCfg<B>;
-  constexpr int NSH = sizeof(T) == 8 ? 3 : 1;
-  __shared__ T sx[3][C::BB];
-  __shared__ float sf[NSH][C::BB];
-  __shared__ int s_flag, s_item;
-  unsigned target = 0;
-  for (int g = 0; g < a.nb; ++g) {
-    const int beg = a.bt_off[g], cnt = a.bt_off[g + 1] - beg;
-    while (true) {
-      if (threadIdx.x == 0) s_item = atomicAdd(&a.work[g], 1);
+__global__ void __launch_bounds__(TileCfg<B>::NT) k_sweep_flow(TiledArgs<T> a, int* flow) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FlowSmem<T, B>& sm = *reinterpret_cast<FlowSmem<T, B>*>(smem_raw);
+  int* const next = flow;            // item counter
+  int* const tile_cnt = flow + 1;    // visits per tile in this sweep
+  const int total = a.nbt + a.ntiles;
+  bool first = true;
+  while (true) {
+    if (threadIdx.x == 0) sm.item = atomicAdd(next, 1);
+    __syncthreads();
+    const int w = sm.item;
+    __syncthreads();
+    if (w >= total) break;
+    if (w < a.nbt) {
+      int I, J, K;
+      unpack_bt(a.bt_list[w], I, J, K);
+      const int g = (I + J + K) % a.nb;
+      const int64_t tIJ = tile_index(a.nb, I, J), tIK = tile_index(a.nb, I, K), tJK = tile_index(a.nb, J, K);
+      const int64_t u1 = (K == J) ? -1 : tIK, u2 = (I == J) ? -1 : tJK;
+      if (threadIdx.x == 0) sm.flag = wait_tiles(tile_cnt, tIJ, u1, u2, g, a.ctl, a.timeout_ns, g);
       __syncthreads();
-      const int k = s_item;
+      if (!sm.flag) return;
+      flow_block_triple<T, UNITW, B, false>(a, w, I, J, K, sm);
+      if (first && (int)blockIdx.x == a.skip_cta) return;   // fault injection: never release
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(tile_cnt + tIJ, 1);
+        if (u1 >= 0) atomicAdd(tile_cnt + u1, 1);
+        if (u2 >= 0) atomicAdd(tile_cnt + u2, 1);
+      }
+    } else {
+      const int tl = w - a.nbt;
+      if (threadIdx.x == 0) sm.flag = wait_tiles(tile_cnt, tl, -1, -1, a.nb, a.ctl, a.timeout_ns, a.nb);
       __syncthreads();
-      if (k >= cnt) break;
-      filtered_block_triple<T, UNITW, B>(a, beg + k, sx[0], sx[1], sx[2], sf[0], sf[NSH == 3 ? 1 : 0],
-                                         sf[NSH == 3 ? 2 : 0]);
+      if (!sm.flag) return;
+      flow_pair_tile<T, B, false>(a, tl);
     }
-    target += gridDim.x;
-    const bool skip = (g == 0) && ((int)blockIdx.x == a.skip_cta);
-    if (!grid_barrier(a.ctl, target, a.timeout_ns, g, skip, &s_flag)) return;
+    first = false;
   }
-  tiled_pair_phase<T, false, B>(a);
+}
+
+// The same dataflow sweep with one warp per work item: the warps of a CTA
+// are independent (each has its own shared-memory slice and synchronizes
+// only with __syncwarp), so no CTA-wide barrier is ever needed.
+template <typename T, bool UNITW, int B>
+__global__ void __launch_bounds__(256) k_sweep_warpflow(TiledArgs<T> a, int* flow) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  FlowSmem<T, B>& sm = reinterpret_cast<FlowSmem<T, B>*>(smem_raw)[wid];
+  int* const next = flow;
+  int* const tile_cnt = flow + 1;
+  const int total = a.nbt + a.ntiles;
+  bool first = true;
+  while (true) {
+    int w = 0;
+    if (lane == 0) w = atomicAdd(next, 1);
+    w = __shfl_sync(0xffffffffu, w, 0);
+    if (w >= total) break;
+    if (w < a.nbt) {
+      int I, J, K;
+      unpack_bt(a.bt_list[w], I, J, K);
+      const int g = (I + J + K) % a.nb;
+      const int64_t tIJ = tile_index(a.nb, I, J), tIK = tile_index(a.nb, I, K), tJK = tile_index(a.nb, J, K);
+      const int64_t u1 = (K == J) ? -1 : tIK, u2 = (I == J) ? -1 : tJK;
+      int ok = 0;
+      if (lane == 0) ok = wait_tiles(tile_cnt, tIJ, u1, u2, g, a.ctl, a.timeout_ns, g);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) return;
+      flow_block_triple<T, UNITW, B, true>(a, w, I, J, K, sm);
+      if (first && (int)blockIdx.x == a.skip_cta) return;   // fault injection: never release
+      if (lane == 0) {
+        __threadfence();
+        atomicAdd(tile_cnt + tIJ, 1);
+        if (u1 >= 0) atomicAdd(tile_cnt + u1, 1);
+        if (u2 >= 0) atomicAdd(tile_cnt + u2, 1);
+      }
+    } else {
+      const int tl = w - a.nbt;
+      int ok = 0;
+      if (lane == 0) ok = wait_tiles(tile_cnt, tl, -1, -1, a.nb, a.ctl, a.timeout_ns, a.nb);
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) return;
+      flow_pair_tile<T, B, true>(a, tl);
+      __syncwarp();
+    }
+    first = false;
+  }
 }
 
 // Rebuild the nonzero bits from the dual store (after the store was written

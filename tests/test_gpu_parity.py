@@ -67,17 +67,67 @@ def test_exact_mode_is_bitwise_equal(n, tile, weighted):
         _assert_state_equal(_gpu_state(s), o)
 
 
+@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("n,weighted", [(60, False), (61, True), (3, False), (4, True), (33, False)])
+def test_paper_schedules_exact_bitwise(schedule, n, weighted):
+    """Schedules 0 (the paper's diagonal listing) and 1 (sum mod n) on the
+    GPU, row by row as Algorithm 1 states it: bit-identical to the oracle."""
+    d, w, _ = planted_partition(n, 3, 0.8, 0.1, seed=n, weights=(0.5, 2.0) if weighted else None)
+    o = oracle.State(n, d, w, 0.2)
+    with _solver(n, d, w, eps=0.2, schedule=schedule, exact=True) as s:
+        o.sweep(schedule)
+        s.sweep(1)
+        _assert_state_equal(_gpu_state(s), o)
+        o.sweep(schedule)
+        o.sweep(schedule)
+        s.sweep(2)
+        _assert_state_equal(_gpu_state(s), o)
+        assert s.check()["max_violation"] == o.max_violation()
+
+
+@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("n,weighted", [(80, True), (150, False)])
+def test_paper_schedules_fused_one_sweep(schedule, n, weighted):
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=n, weights=(0.5, 2.0) if weighted else None)
+    o = oracle.State(n, d, w, 0.2)
+    for _ in range(3):
+        o.sweep(schedule)
+    with _solver(n, d, w, eps=0.2, schedule=schedule) as s:
+        s.set_state(o.x, o.f, o.ytri, o.ypair)
+        s.sweep(1)
+        o.sweep(schedule)
+        _assert_state_close(_gpu_state(s), o, TOL_SWEEP)
+        T = n * (n - 1) * (n - 2) // 6
+        full, _ = s.get_duals()
+        part, _ = s.get_duals(T // 3, 500, pairs=False)
+        np.testing.assert_array_equal(part, full[3 * (T // 3): 3 * (T // 3 + 500)])
+
+
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_paper_schedules_converge_planted60(schedule):
+    n, d, w, _ = workload("planted60")
+    o = oracle.State(n, d, w, 0.2)
+    ko = o.solve(1e-4, 5000, schedule=schedule, check_every=1)
+    with _solver(n, d, w, eps=0.2, schedule=schedule, check_every=1) as s:
+        conv, kg = s.solve(1e-4, 5000)
+        st = s.check()
+    assert conv and kg == ko
+    assert abs(st["lp_objective"] - o.objectives()["lp"]) <= 1e-6 * o.objectives()["lp"]
+
+
 # ---------------------------------------------------------------- fused form
 
+@pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("n,tile,weighted,pre", [(60, 16, False, 3), (61, 16, True, 5),
-                                                 (200, 16, False, 2), (150, 32, True, 2),
-                                                 (90, 8, True, 4)])
-def test_fused_one_sweep_from_identical_state(n, tile, weighted, pre):
+                                                 (200, 16, False, 2), (150, 8, True, 2),
+                                                 (90, 8, True, 4), (203, 8, False, 6)])
+def test_fused_one_sweep_from_identical_state(n, tile, weighted, pre, variant):
+    """variant 1: one CTA per block triple; 2: one warp per block triple."""
     d, w, _ = chung_lu(n, 2.5, 8.0, seed=n, weights=(0.5, 2.0) if weighted else None)
     o = oracle.State(n, d, w, 0.2)
     for _ in range(pre):
         o.sweep(2, tile)
-    with _solver(n, d, w, eps=0.2, tile=tile) as s:
+    with _solver(n, d, w, eps=0.2, tile=tile, variant=variant) as s:
         s.set_state(o.x, o.f, o.ytri, o.ypair)
         _assert_state_close(_gpu_state(s), o, 1e-15)   # round trip of the state
         s.sweep(1)
@@ -115,6 +165,20 @@ def test_fused_near_tight_rows(n, tile, weighted):
         _assert_state_close(_gpu_state(s), o, TOL_SWEEP)
         st = s.check()      # x now differs from the oracle's by rounding only
         assert st["max_violation"] == pytest.approx(o.max_violation(), abs=1e-12)
+
+
+@pytest.mark.parametrize("n,tile,weighted", [(150, 32, True), (97, 32, False)])
+def test_fused_tile32_cta_kernel(n, tile, weighted):
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=n, weights=(0.5, 2.0) if weighted else None)
+    o = oracle.State(n, d, w, 0.2)
+    for _ in range(2):
+        o.sweep(2, tile)
+    with _solver(n, d, w, eps=0.2, tile=tile) as s:
+        s.set_state(o.x, o.f, o.ytri, o.ypair)
+        s.sweep(2)
+        o.sweep(2, tile)
+        o.sweep(2, tile)
+        _assert_state_close(_gpu_state(s), o, 2 * TOL_SWEEP)
 
 
 def test_fused_matches_over_many_sweeps_planted60():
