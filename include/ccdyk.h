@@ -91,6 +91,9 @@ typedef struct cc_opts {
   int32_t variant;          /* fused-form sweep kernel: 0 or 1 = one CTA per
                                block triple (default), 2 = one warp per block
                                triple (tile <= 16) */
+  double refine_at;         /* CC_PREC_FP32_REFINE: cc_solve leaves FP32 when
+                               the violation is <= max(tol, refine_at) or stops
+                               decreasing between checks; default 1e-5 */
 } cc_opts;
 
 typedef struct cc_stats {
@@ -103,6 +106,8 @@ typedef struct cc_stats {
   double dual_objective;   /* -b^T y - (eps/2) v^T W v (valid while v = v0 - W^-1 A^T y / eps) */
   double gap;              /* qp_primal - dual_objective */
   double last_sweep_ms;    /* device time of the most recent sweep launch */
+  int64_t fp32_sweeps;     /* sweeps run with FP32 state (CC_PREC_FP32_REFINE) */
+  int32_t state_fp32;      /* 1 while the state is held in FP32 */
 } cc_stats;
 
 typedef struct cc_handle cc_handle;
@@ -147,6 +152,21 @@ int cc_get_duals(cc_handle* h, double* y_tri, double* y_pair, int64_t tri_first,
  * checkpoint/resume and warm starts. */
 int cc_set_state(cc_handle* h, const double* x, const double* f, const double* y_tri,
                  const double* y_pair);
+
+/* End the FP32 bulk phase of CC_PREC_FP32_REFINE now: the duals are
+ * converted to FP64 and x, f are rebuilt from them in FP64 through the
+ * identity v = v0 - W^{-1} A^T y / eps that Dykstra's method keeps
+ * (Algorithm 1), so that FP32 rounding in x does not carry into the
+ * refinement.  cc_solve does this by itself when the FP32 state first meets
+ * the tolerance.  No-op for FP64 state. */
+int cc_refine_fp64(cc_handle* h);
+
+/* Warm start: set the duals (y_tri: 3 C(n,3) doubles, y_pair: 2P doubles,
+ * host, canonical order, each >= 0) and rebuild x, f from them through
+ * v = v0 - W^{-1} A^T y / eps.  Dykstra's method converges from any
+ * nonnegative duals made consistent this way.  Tiled schedule, fused form,
+ * FP64 state. */
+int cc_set_duals(cc_handle* h, const double* y_tri, const double* y_pair);
 
 /* Counters of the last check plus sweeps and last sweep time (no device work). */
 int cc_get_stats(cc_handle* h, cc_stats* st);

@@ -17,14 +17,14 @@ from ._native import (CCError, CC_OK, CC_ERR_ARG, CC_ERR_OOM, CC_ERR_CUDA, CC_ER
                       CC_SCHED_SUMMOD, CC_SCHED_TILED, CC_PREC_FP64, CC_PREC_FP32_REFINE,
                       cc_opts_default, cc_create, cc_create_device, cc_sweep, cc_check, cc_solve,
                       cc_get_x, cc_get_duals, cc_set_state, cc_get_stats, cc_device_bytes,
-                      cc_destroy, cc_last_error)
+                      cc_destroy, cc_last_error, cc_refine_fp64, cc_set_duals, cc_check_noalloc)
 from .buildlib import build
 
 __all__ = [
     "Solver", "CCError", "build", "num_pairs", "num_triplets",
     "cc_opts_default", "cc_create", "cc_create_device", "cc_sweep", "cc_check", "cc_solve",
     "cc_get_x", "cc_get_duals", "cc_set_state", "cc_get_stats", "cc_device_bytes",
-    "cc_destroy", "cc_last_error",
+    "cc_destroy", "cc_last_error", "cc_refine_fp64", "cc_set_duals", "cc_check_noalloc",
 ]
 
 SCHEDULES = {"diagonal": CC_SCHED_DIAGONAL, "summod": CC_SCHED_SUMMOD, "tiled": CC_SCHED_TILED}
@@ -69,7 +69,8 @@ class Solver:
 
     def __init__(self, n, d, w, eps=0.2, schedule="tiled", tile=16, precision="fp64",
                  exact=False, check_every=10, device=0, stream=None, torch_alloc=True,
-                 barrier_timeout_s=2.0, grid=0, debug_skip_cta=-1, on_device=False, variant=0):
+                 barrier_timeout_s=2.0, grid=0, debug_skip_cta=-1, on_device=False, variant=0,
+                 refine_at=1e-5):
         o = cc_opts_default()
         o.eps = float(eps)
         o.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
@@ -82,6 +83,7 @@ class Solver:
         o.grid = int(grid)
         o.debug_skip_cta = int(debug_skip_cta)
         o.variant = int(variant)
+        o.refine_at = float(refine_at)
         self._alloc = None
         try:
             import torch
@@ -139,6 +141,13 @@ class Solver:
     def set_state(self, x, f, y_tri, y_pair) -> None:
         c = lambda a: np.ascontiguousarray(a, dtype=np.float64)
         cc_set_state(self.h, c(x), c(f), c(y_tri), c(y_pair))
+
+    def refine_fp64(self) -> None:
+        cc_refine_fp64(self.h)
+
+    def set_duals(self, y_tri, y_pair) -> None:
+        c = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+        cc_set_duals(self.h, c(y_tri), c(y_pair))
 
     def stats(self) -> dict:
         return cc_get_stats(self.h).as_dict()

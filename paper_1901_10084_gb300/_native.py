@@ -48,6 +48,7 @@ class cc_opts(ctypes.Structure):
         ("grid", ctypes.c_int32),
         ("debug_skip_cta", ctypes.c_int32),
         ("variant", ctypes.c_int32),
+        ("refine_at", ctypes.c_double),
     ]
 
 
@@ -62,6 +63,8 @@ class cc_stats(ctypes.Structure):
         ("dual_objective", ctypes.c_double),
         ("gap", ctypes.c_double),
         ("last_sweep_ms", ctypes.c_double),
+        ("fp32_sweeps", ctypes.c_int64),
+        ("state_fp32", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -70,7 +73,8 @@ class cc_stats(ctypes.Structure):
 
 EXPORTS = ("cc_opts_default", "cc_create", "cc_create_device", "cc_sweep", "cc_check",
            "cc_solve", "cc_get_x", "cc_get_duals", "cc_set_state", "cc_get_stats",
-           "cc_device_bytes", "cc_destroy", "cc_last_error", "cc_check_noalloc")
+           "cc_device_bytes", "cc_destroy", "cc_last_error", "cc_check_noalloc",
+           "cc_refine_fp64", "cc_set_duals")
 
 _lib = None
 _lock = threading.Lock()
@@ -122,6 +126,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         lib.cc_destroy.restype = None
         lib.cc_last_error.argtypes = [H]
         lib.cc_last_error.restype = ctypes.c_char_p
+        lib.cc_refine_fp64.argtypes = [H]
+        lib.cc_refine_fp64.restype = ctypes.c_int
+        lib.cc_set_duals.argtypes = [H, dp, dp]
+        lib.cc_set_duals.restype = ctypes.c_int
         vp = ctypes.c_void_p
         lib.cc_check_noalloc.argtypes = [i64, ctypes.c_double, vp, vp, vp, vp, vp, vp, vp]
         lib.cc_check_noalloc.restype = ctypes.c_int
@@ -199,6 +207,14 @@ def cc_get_duals(h, y_tri, y_pair, tri_first: int = 0, tri_count: int = 0) -> No
 
 def cc_set_state(h, x, f, y_tri, y_pair) -> None:
     _check(load().cc_set_state(h, _dp(x), _dp(f), _dp(y_tri), _dp(y_pair)), h)
+
+
+def cc_refine_fp64(h) -> None:
+    _check(load().cc_refine_fp64(h), h)
+
+
+def cc_set_duals(h, y_tri, y_pair) -> None:
+    _check(load().cc_set_duals(h, _dp(y_tri), _dp(y_pair)), h)
 
 
 def cc_get_stats(h) -> cc_stats:

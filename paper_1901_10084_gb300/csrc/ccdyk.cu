@@ -39,8 +39,11 @@ struct cc_handle {
   // device state (element type double, or float while fp32)
   void* x = nullptr;
   void* f = nullptr;
-  void* d = nullptr;
+  void* d = nullptr;         // current precision (aliases d64 in FP64)
   void* winv = nullptr;
+  double* d64 = nullptr;     // FP64 problem data, kept for the whole solve
+  double* winv64 = nullptr;
+  int64_t fp32_sweeps = 0;
   void* zt = nullptr;
   void* zp = nullptr;
   int64_t tile_elems = 0;   // ntiles * B * B
@@ -482,8 +485,15 @@ int create_common(cc_handle** out, int64_t n, const double* d_dev, const double*
   const size_t te = (size_t)h->tile_elems;
   h->x = dalloc(h, te * h->esz);
   h->f = dalloc(h, te * h->esz);
-  h->d = dalloc(h, te * h->esz);
-  h->winv = dalloc(h, te * h->esz);
+  h->d64 = (double*)dalloc(h, te * sizeof(double));
+  h->winv64 = (double*)dalloc(h, te * sizeof(double));
+  if (h->fp32) {
+    h->d = dalloc(h, te * sizeof(float));
+    h->winv = dalloc(h, te * sizeof(float));
+  } else {
+    h->d = h->d64;
+    h->winv = h->winv64;
+  }
   h->zp = dalloc(h, te * 2 * h->esz);
   h->zt = dalloc(h, (size_t)h->zt_elems * h->esz);
   h->ctl = (Ctl*)dalloc(h, sizeof(Ctl));
@@ -496,20 +506,19 @@ int create_common(cc_handle** out, int64_t n, const double* d_dev, const double*
   }
   h->part_cap = std::max(8 * h->sms, 64);
   h->part = (double*)dalloc(h, (size_t)h->part_cap * 6 * sizeof(double));  // maxima, then 5 sums each
-  if (!h->x || !h->f || !h->d || !h->winv || !h->zp || !h->zt || !h->ctl || !h->part)
+  if (!h->x || !h->f || !h->d64 || !h->winv64 || !h->d || !h->winv || !h->zp || !h->zt || !h->ctl || !h->part)
     return fail(h, CC_ERR_OOM, "device state");
   CK(h, cudaMallocHost((void**)&h->h_pin, 64 * sizeof(double)));
   CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->st));
-  CK(h, cudaMemsetAsync(h->d, 0, te * h->esz, h->st));
+  CK(h, cudaMemsetAsync(h->d64, 0, te * sizeof(double), h->st));
+  k_fill<double><<<grid_for(h, te, 256), 256, 0, h->st>>>(h->winv64, te, 1.0);
+  k_load_problem<double><<<grid_for(h, h->P, 256), 256, 0, h->st>>>(d_dev, w_dev, (int)n, h->nb, h->B, h->d64,
+                                                                     h->winv64);
   if (h->fp32) {
-    k_fill<float><<<grid_for(h, te, 256), 256, 0, h->st>>>((float*)h->winv, te, 1.0f);
-    k_load_problem<float><<<grid_for(h, h->P, 256), 256, 0, h->st>>>(d_dev, w_dev, (int)n, h->nb, h->B,
-                                                                      (float*)h->d, (float*)h->winv);
+    k_convert<double, float><<<grid_for(h, te, 256), 256, 0, h->st>>>(h->d64, (float*)h->d, te);
+    k_convert<double, float><<<grid_for(h, te, 256), 256, 0, h->st>>>(h->winv64, (float*)h->winv, te);
     rc = init_state<float>(h);
   } else {
-    k_fill<double><<<grid_for(h, te, 256), 256, 0, h->st>>>((double*)h->winv, te, 1.0);
-    k_load_problem<double><<<grid_for(h, h->P, 256), 256, 0, h->st>>>(d_dev, w_dev, (int)n, h->nb, h->B,
-                                                                       (double*)h->d, (double*)h->winv);
     rc = init_state<double>(h);
   }
   if (rc) return rc;
@@ -530,6 +539,8 @@ int check_opts(const cc_opts& o) {
   if (o.precision != CC_PREC_FP64 && o.precision != CC_PREC_FP32_REFINE)
     return fail(nullptr, CC_ERR_ARG, "unknown precision");
   if (o.exact && o.precision != CC_PREC_FP64) return fail(nullptr, CC_ERR_ARG, "exact mode needs FP64");
+  if (o.precision == CC_PREC_FP32_REFINE && o.schedule != CC_SCHED_TILED)
+    return fail(nullptr, CC_ERR_ARG, "the FP32 bulk form runs on the tiled schedule");
   if (o.check_every < 1) return fail(nullptr, CC_ERR_ARG, "check_every must be >= 1");
   if (!(o.barrier_timeout_s > 0.0)) return fail(nullptr, CC_ERR_ARG, "barrier_timeout_s must be > 0");
   if ((o.alloc == nullptr) != (o.free == nullptr)) return fail(nullptr, CC_ERR_ARG, "alloc and free go together");
@@ -563,6 +574,61 @@ int new_handle(cc_handle** out, int64_t n, const cc_opts* opts, cc_handle** hp) 
 
 }  // namespace
 
+// x, f <- v0 - W^{-1} A^T z from the FP64 duals (tiled schedule, fused form).
+int resync_fp64(cc_handle* h) {
+  const int B = h->B;
+  double* x = (double*)h->x;
+  CK(h, cudaMemsetAsync(x, 0, (size_t)h->tile_elems * sizeof(double), h->st));
+  CK(h, cudaMemsetAsync(&h->ctl->arrive, 0, sizeof(unsigned), h->st));
+  const double* zt = (const double*)h->zt;
+  const uint32_t* mask = h->mask;
+  int nb = h->nb;
+  int n = (int)h->n;
+  const int* bl = h->bt_list;
+  const int* bo = h->bt_off;
+  Ctl* ctl = h->ctl;
+  long long tns = (long long)(h->o.barrier_timeout_s * 1e9);
+  void* args[] = {(void*)&zt, (void*)&mask, (void*)&x, &n, &nb, (void*)&bl, (void*)&bo, (void*)&ctl, &tns};
+  void* k = B == 8 ? (void*)k_resync_metric<8> : B == 16 ? (void*)k_resync_metric<16> : (void*)k_resync_metric<32>;
+  const int threads = threads_for_tile(B);
+  int per_sm = 0;
+  CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0));
+  const int grid = std::max(1, std::min(per_sm * h->sms, std::max(1, h->max_bt_phase)));
+  CK(h, cudaLaunchCooperativeKernel(k, grid, threads, args, 0, h->st));
+  k_resync_finish<<<grid_for(h, h->tile_elems, 256), 256, 0, h->st>>>(x, (double*)h->f, h->winv64,
+                                                                       (const double*)h->zp, h->ntiles, B * B,
+                                                                       h->o.eps);
+  CK(h, cudaGetLastError());
+  return read_ctl_error(h);
+}
+
+// Leave the FP32 bulk phase: duals to FP64, x and f rebuilt from them in FP64.
+int switch_to_fp64(cc_handle* h) {
+  if (!h->fp32) return CC_OK;
+  int rc = read_ctl_error(h);
+  if (rc) return rc;
+  const size_t te = (size_t)h->tile_elems;
+  double* zt = (double*)dalloc(h, (size_t)h->zt_elems * sizeof(double));
+  double* zp = (double*)dalloc(h, te * 2 * sizeof(double));
+  double* x = (double*)dalloc(h, te * sizeof(double));
+  double* f = (double*)dalloc(h, te * sizeof(double));
+  if (!zt || !zp || !x || !f) {
+    dfree(h, zt); dfree(h, zp); dfree(h, x); dfree(h, f);
+    return fail(h, CC_ERR_OOM, "FP64 refinement state");
+  }
+  k_convert<float, double><<<grid_for(h, h->zt_elems, 256), 256, 0, h->st>>>((const float*)h->zt, zt, h->zt_elems);
+  k_convert<float, double><<<grid_for(h, 2 * te, 256), 256, 0, h->st>>>((const float*)h->zp, zp, 2 * (int64_t)te);
+  CK(h, cudaGetLastError());
+  CK(h, cudaStreamSynchronize(h->st));
+  dfree(h, h->zt); dfree(h, h->zp); dfree(h, h->x); dfree(h, h->f); dfree(h, h->d); dfree(h, h->winv);
+  h->zt = zt; h->zp = zp; h->x = x; h->f = f; h->d = h->d64; h->winv = h->winv64;
+  h->fp32 = false;
+  h->esz = 8;
+  rc = resync_fp64(h);
+  if (rc) return rc;
+  return configure_sweep(h);
+}
+
 // Message for cc_last_error(NULL) from entry points outside this file.
 void ccd_set_global_error(const char* msg) { g_create_error = msg ? msg : ""; }
 
@@ -587,6 +653,8 @@ void cc_opts_default(cc_opts* o) {
   o->alloc_ctx = nullptr;
   o->grid = 0;
   o->debug_skip_cta = -1;
+  o->variant = 0;
+  o->refine_at = 1e-5;
 }
 
 int cc_create_device(cc_handle** out, int64_t n, const double* d_dev, const double* w_dev, const cc_opts* opts) {
@@ -651,6 +719,7 @@ int cc_sweep(cc_handle* h, int64_t k) {
       h->ev_recorded = true;
     }
     h->sweeps++;
+    if (h->fp32) h->fp32_sweeps++;
   }
   return CC_OK;
 }
@@ -669,8 +738,8 @@ int cc_check(cc_handle* h, cc_stats* st) {
 #define LAUNCH_CHECK(T, BV)                                                                                   \
   k_maxviol_tiled<T, BV><<<gtri, threads_for_tile(BV), 0, h->st>>>((const T*)h->x, (int)h->n, h->nb,      \
                                                                     h->bt_list, h->nbt, pm);                \
-  k_pairsums_tiled<T, BV><<<gpair, 256, 0, h->st>>>((const T*)h->x, (const T*)h->f, (const T*)h->d,        \
-                                                    (const T*)h->winv, (const T*)h->zp, h->tile_list,      \
+  k_pairsums_tiled<T, BV><<<gpair, 256, 0, h->st>>>((const T*)h->x, (const T*)h->f, h->d64,                 \
+                                                    h->winv64, (const T*)h->zp, h->tile_list,              \
                                                     h->ntiles, (int)h->n, yscale, ps);
   if (h->fp32) {
     if (B == 8) { LAUNCH_CHECK(float, 8) } else if (B == 16) { LAUNCH_CHECK(float, 16) } else { LAUNCH_CHECK(float, 32) }
@@ -694,6 +763,8 @@ int cc_check(cc_handle* h, cc_stats* st) {
   }
   cc_stats& s = h->last;
   s.sweeps = h->sweeps;
+  s.fp32_sweeps = h->fp32_sweeps;
+  s.state_fp32 = h->fp32 ? 1 : 0;
   s.max_violation = mv;
   s.pair_violation = pv;
   s.lp_objective = lp;
@@ -715,6 +786,7 @@ int cc_solve(cc_handle* h, double tol, int64_t max_sweeps, int64_t* sweeps_done)
   if (max_sweeps < 0) return fail(h, CC_ERR_ARG, "max_sweeps must be >= 0");
   int64_t done = 0;
   if (sweeps_done) *sweeps_done = 0;
+  double prev_fp32 = INFINITY;
   while (done < max_sweeps) {
     int64_t k = std::min<int64_t>(h->o.check_every, max_sweeps - done);
     int rc = cc_sweep(h, k);
@@ -724,7 +796,22 @@ int cc_solve(cc_handle* h, double tol, int64_t max_sweeps, int64_t* sweeps_done)
     cc_stats s;
     rc = cc_check(h, &s);
     if (rc) return rc;
-    if (s.max_violation <= tol) return CC_OK;
+    if (!h->fp32) {
+      if (s.max_violation <= tol) return CC_OK;
+      continue;
+    }
+    // FP32 bulk phase: refine in FP64 (from the converted duals) once the
+    // violation is small enough for FP32 or stops decreasing
+    const bool small = s.max_violation <= std::max(tol, h->o.refine_at);
+    const bool stalled = s.max_violation > 0.99 * prev_fp32;
+    prev_fp32 = s.max_violation;
+    if (small || stalled) {
+      rc = switch_to_fp64(h);
+      if (rc) return rc;
+      rc = cc_check(h, &s);
+      if (rc) return rc;
+      if (s.max_violation <= tol) return CC_OK;
+    }
   }
   return fail(h, CC_ERR_NOT_CONVERGED, "max_sweeps reached before the tolerance");
 }
@@ -850,10 +937,40 @@ int cc_set_state(cc_handle* h, const double* x, const double* f, const double* y
   return CC_OK;
 }
 
+int cc_refine_fp64(cc_handle* h) {
+  if (!h) return fail(nullptr, CC_ERR_ARG, "handle is NULL");
+  CK(h, cudaSetDevice(h->dev));
+  return switch_to_fp64(h);
+}
+
+int cc_set_duals(cc_handle* h, const double* y_tri, const double* y_pair) {
+  if (!h) return fail(nullptr, CC_ERR_ARG, "handle is NULL");
+  if (!y_tri || !y_pair) return fail(h, CC_ERR_ARG, "y_tri and y_pair are required");
+  if (h->o.schedule != CC_SCHED_TILED || h->o.exact || h->fp32)
+    return fail(h, CC_ERR_UNSUPPORTED, "cc_set_duals needs the tiled schedule, fused form, FP64 state");
+  CK(h, cudaSetDevice(h->dev));
+  int rc = read_ctl_error(h);
+  if (rc) return rc;
+  rc = move_duals(h, const_cast<double*>(y_tri), const_cast<double*>(y_pair), 0, h->T3, 1);
+  if (rc) return rc;
+  const int g2 = grid_for(h, h->mask_words, 256);
+  if (h->B == 8) k_rebuild_mask<double, 8><<<g2, 256, 0, h->st>>>((const double*)h->zt, h->mask, h->mask_words);
+  else if (h->B == 16) k_rebuild_mask<double, 16><<<g2, 256, 0, h->st>>>((const double*)h->zt, h->mask, h->mask_words);
+  else k_rebuild_mask<double, 32><<<g2, 256, 0, h->st>>>((const double*)h->zt, h->mask, h->mask_words);
+  CK(h, cudaGetLastError());
+  rc = resync_fp64(h);
+  if (rc) return rc;
+  h->sweeps = 0;
+  h->fp32_sweeps = 0;
+  return CC_OK;
+}
+
 int cc_get_stats(cc_handle* h, cc_stats* st) {
   if (!h || !st) return fail(h, CC_ERR_ARG, "NULL argument");
   *st = h->last;
   st->sweeps = h->sweeps;
+  st->fp32_sweeps = h->fp32_sweeps;
+  st->state_fp32 = h->fp32 ? 1 : 0;
   return CC_OK;
 }
 

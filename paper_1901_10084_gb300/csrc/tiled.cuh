@@ -688,7 +688,7 @@ __global__ void __launch_bounds__(TileCfg<B>::NT) k_maxviol_tiled(const T* __res
 // by = sum d (y+ - y-) (y = yscale * stored dual), pv = max pair violation.
 template <typename T, int B>
 __global__ void __launch_bounds__(256) k_pairsums_tiled(const T* __restrict__ x, const T* __restrict__ f,
-                                                         const T* __restrict__ d, const T* __restrict__ winv,
+                                                         const double* __restrict__ d, const double* __restrict__ winv,
                                                          const T* __restrict__ zp, const int* __restrict__ tile_list,
                                                          int ntiles, int n, double yscale, double* part) {
   using C = TileCfg<B>;
@@ -702,7 +702,7 @@ __global__ void __launch_bounds__(256) k_pairsums_tiled(const T* __restrict__ x,
     const int I = pk & 0xffff, J = pk >> 16;
     const int la = slot / B, lb = slot % B;
     if (!((I < J || la < lb) && J * B + lb < n)) continue;
-    const double xv = x[e], fv = f[e], dv = d[e], wv = 1.0 / (double)winv[e];
+    const double xv = x[e], fv = f[e], dv = d[e], wv = 1.0 / winv[e];
     const double yp = yscale * (double)zp[(int64_t)tl * 2 * C::BB + slot];
     const double ym = yscale * (double)zp[(int64_t)tl * 2 * C::BB + C::BB + slot];
     lp += wv * fabs(xv - dv);
@@ -828,6 +828,104 @@ __global__ void k_pair_duals_tiled(T* zp, int n, int nb, int B, double* buf, dou
       zp[e + BB] = (T)(buf[2 * p + 1] / scale);
     }
   }
+}
+
+// ------------------------------------------------------------ resync
+//
+// Dykstra keeps v = v0 - W^{-1} A^T z (z = y/eps) at every step.  After the
+// duals change precision (FP32 bulk -> FP64 refinement) or are set from
+// outside, x and f are rebuilt from that identity in FP64:
+//   acc_p = sum over metric rows of z_r * (+1 if p is a leg, -1 if p is the
+//           hypotenuse),
+//   x_p = w_p^-1 (acc_p - z+_p + z-_p),   f_p = -1/eps + w_p^-1 (z+_p + z-_p).
+// Pass 1 visits the block triples phase by phase (tiles of one phase are
+// disjoint) and inside a block triple sub-phase by sub-phase, so the sums are
+// formed in one fixed order (deterministic); block triples without a nonzero
+// dual are skipped through the bitmask.
+template <int B>
+__global__ void __launch_bounds__(TileCfg<B>::NT) k_resync_metric(const double* __restrict__ zt,
+                                                                   const uint32_t* __restrict__ mask, double* acc,
+                                                                   int n, int nb, const int* __restrict__ bt_list,
+                                                                   const int* __restrict__ bt_off, Ctl* ctl,
+                                                                   long long timeout_ns) {
+  using C = TileCfg<B>;
+  using M = MaskCfg<B>;
+  __shared__ double sx[3][C::BB];
+  __shared__ int s_flag;
+  unsigned target = 0;
+  const int lane = threadIdx.x & 31;
+  for (int g = 0; g < nb; ++g) {
+    for (int w = bt_off[g] + (int)blockIdx.x; w < bt_off[g + 1]; w += gridDim.x) {
+      const uint32_t* mb = mask + (int64_t)w * M::PER_BT;
+      int any = 0;
+      for (int e = threadIdx.x; e < M::PER_BT; e += C::NT) any |= (mb[e] != 0u);
+      if (!__syncthreads_or(any)) continue;
+      int I, J, K;
+      unpack_bt(bt_list[w], I, J, K);
+      const int64_t oIJ = tile_index(nb, I, J) * C::BB, oIK = tile_index(nb, I, K) * C::BB,
+                    oJK = tile_index(nb, J, K) * C::BB;
+      const bool kj = (K == J), ij = (I == J);
+      double* pIJ = sx[0];
+      double* pIK = kj ? sx[0] : sx[1];
+      double* pJK = ij ? pIK : sx[2];
+      for (int e = threadIdx.x; e < C::BB; e += C::NT) {
+        sx[0][e] = ld_l2(acc + oIJ + e);
+        if (!kj) sx[1][e] = ld_l2(acc + oIK + e);
+        if (!ij) sx[2][e] = ld_l2(acc + oJK + e);
+      }
+      __syncthreads();
+      const double* zb = zt + (int64_t)w * (3 * B * C::BB);
+      for (int t = 0; t < B; ++t) {
+        for (int q = 0; q < C::SPT; ++q) {
+          const int slot = threadIdx.x + q * C::NT;
+          const int la = slot / B, lb = slot % B, lc = (t - la - lb) & (B - 1);
+          const int qw = t * (3 * M::WPR) + (slot >> 5);
+          const bool b0 = (mb[qw] >> lane) & 1u, b1 = (mb[qw + M::WPR] >> lane) & 1u,
+                     b2 = (mb[qw + 2 * M::WPR] >> lane) & 1u;
+          if (b0 | b1 | b2) {
+            const double* zs = zb + (int64_t)t * (3 * C::BB) + slot;
+            const double z0 = b0 ? zs[0] : 0.0, z1 = b1 ? zs[C::BB] : 0.0, z2 = b2 ? zs[2 * C::BB] : 0.0;
+            const int eij = la * B + lb, eik = la * B + lc, ejk = lb * B + lc;
+            double aij = pIJ[eij], aik = pIK[eik], ajk = pJK[ejk];
+            aij = ((aij - z0) + z1) + z2;   // hypotenuse of row 0, leg of rows 1 and 2
+            aik = ((aik + z0) - z1) + z2;   // hypotenuse of row 1
+            ajk = ((ajk + z0) + z1) - z2;   // hypotenuse of row 2
+            pIJ[eij] = aij;
+            pIK[eik] = aik;
+            pJK[ejk] = ajk;
+          }
+        }
+        __syncthreads();
+      }
+      for (int e = threadIdx.x; e < C::BB; e += C::NT) {
+        acc[oIJ + e] = sx[0][e];
+        if (!kj) acc[oIK + e] = sx[1][e];
+        if (!ij) acc[oJK + e] = sx[2][e];
+      }
+      __syncthreads();
+    }
+    target += gridDim.x;
+    if (!grid_barrier(ctl, target, timeout_ns, g, false, &s_flag)) return;
+  }
+}
+
+// Pass 2: x and f from acc and the pair duals (in place: acc is x).
+__global__ void k_resync_finish(double* x, double* f, const double* __restrict__ winv,
+                                const double* __restrict__ zp, int64_t ntiles, int BB, double eps) {
+  const int64_t total = ntiles * BB;
+  const double f0 = -(1.0 / eps);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t tl = e / BB, slot = e % BB;
+    const double zpv = zp[tl * 2 * BB + slot], zmv = zp[tl * 2 * BB + BB + slot];
+    x[e] = winv[e] * ((x[e] - zpv) + zmv);
+    f[e] = f0 + winv[e] * (zpv + zmv);
+  }
+}
+
+template <typename S, typename D>
+__global__ void k_convert(const S* __restrict__ src, D* dst, int64_t count) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (D)src[e];
 }
 
 }  // namespace ccd

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "ccdyk.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(cc_[a-z_]+)\s*\(", src)) - {"cc_alloc_fn", "cc_free_fn"})
+    return sorted(set(re.findall(r"\b(cc_[a-z0-9_]+)\s*\(", src)) - {"cc_alloc_fn", "cc_free_fn"})
 
 
 @pytest.fixture(scope="module")

@@ -1,0 +1,101 @@
+"""FP32 bulk sweeps + FP64 refinement, the resync x = x0 - W^-1 A^T y/eps,
+and warm starts from duals (GPU, through the C ABI)."""
+import numpy as np
+import pytest
+
+import oracle
+from instances import planted_partition, chung_lu, workload
+
+pytestmark = pytest.mark.gpu
+
+
+def _solver(n, d, w, **kw):
+    import paper_1901_10084_gb300 as cc
+    return cc.Solver(n, d, w, **kw)
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1.0))
+
+
+@pytest.mark.parametrize("n,tile,weighted", [(60, 16, False), (90, 8, True), (130, 32, True)])
+def test_resync_rebuilds_x_and_f_from_the_duals(n, tile, weighted):
+    """After FP64 sweeps, setting the same duals back rebuilds x and f from
+    the invariant; they must equal the swept x and f up to rounding."""
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=n, weights=(0.5, 2.0) if weighted else None)
+    with _solver(n, d, w, tile=tile) as s:
+        s.sweep(7)
+        x, f = s.get_x()
+        yt, yp = s.get_duals()
+        s.set_duals(yt, yp)
+        x2, f2 = s.get_x()
+    assert _rel(x2, x) <= 1e-12 and _rel(f2, f) <= 1e-12
+
+
+def test_warm_start_from_oracle_duals_matches_oracle_state():
+    n = 70
+    d, w, _ = planted_partition(n, 3, 0.7, 0.2, seed=3, weights=(0.5, 2.0))
+    o = oracle.State(n, d, w, 0.2)
+    for _ in range(5):
+        o.sweep(2, 16)
+    with _solver(n, d, w, tile=16) as s:
+        s.set_duals(o.ytri, o.ypair)
+        x, f = s.get_x()
+        assert _rel(x, o.x) <= 1e-12 and _rel(f, o.f) <= 1e-12
+        s.sweep(1)
+        o.sweep(2, 16)
+        x, f = s.get_x()
+        assert _rel(x, o.x) <= 1e-12 and _rel(f, o.f) <= 1e-12
+
+
+@pytest.mark.parametrize("n,weighted", [(60, False), (150, True)])
+def test_fp32_sweep_tracks_the_oracle_to_float_precision(n, weighted):
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=n, weights=(0.5, 2.0) if weighted else None)
+    o = oracle.State(n, d, w, 0.2)
+    with _solver(n, d, w, tile=16, precision="fp32_refine") as s:
+        for _ in range(3):
+            o.sweep(2, 16)
+        s.sweep(3)
+        x, f = s.get_x()
+        st = s.check()
+    assert st["state_fp32"] == 1 and st["fp32_sweeps"] == 3
+    assert _rel(x, o.x) <= 1e-5 and _rel(f, o.f) <= 1e-5
+
+
+@pytest.mark.parametrize("name,tile", [("planted60", 16), ("chunglu300", 8)])
+def test_fp32_refine_reaches_the_fp64_solution(name, tile):
+    """Both forms solved to 1e-8: the LP objectives agree to 1e-6 relative
+    (the QP optimum is unique) and the refined state is FP64."""
+    n, d, w, _ = workload(name)
+    with _solver(n, d, w, tile=tile, check_every=5) as a:
+        conv_a, ka = a.solve(1e-8, 20000)
+        sa = a.check()
+        xa, _ = a.get_x()
+    with _solver(n, d, w, tile=tile, check_every=5, precision="fp32_refine") as b:
+        conv_b, kb = b.solve(1e-8, 20000)
+        sb = b.check()
+        xb, _ = b.get_x()
+    assert conv_a and conv_b
+    assert sb["state_fp32"] == 0 and 0 < sb["fp32_sweeps"] < kb
+    assert sb["max_violation"] <= 1e-8
+    assert abs(sb["lp_objective"] - sa["lp_objective"]) <= 1e-6 * abs(sa["lp_objective"])
+    assert np.max(np.abs(xb - xa)) <= 1e-5
+
+
+def test_refine_switch_keeps_the_invariant():
+    n = 120
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=4, weights=(0.5, 2.0))
+    with _solver(n, d, w, tile=16, precision="fp32_refine") as s:
+        s.sweep(10)
+        yt, yp = s.get_duals()
+        s.refine_fp64()
+        assert s.stats()["state_fp32"] == 0
+        x, f = s.get_x()
+        yt2, yp2 = s.get_duals()
+    # duals are converted exactly; x and f equal the invariant evaluated by the oracle's dense rows
+    np.testing.assert_array_equal(yt2, yt)
+    np.testing.assert_array_equal(yp2, yp)
+    from oracle import dense
+    if n <= 130:
+        r = dense.invariant_residual(n, d, w, 0.2, x, f, yt2, yp2)
+        assert r <= 1e-12
