@@ -90,10 +90,22 @@ typedef struct cc_opts {
                                CC_ERR_TIMEOUT */
   int32_t variant;          /* fused-form sweep kernel: 0 or 1 = one CTA per
                                block triple (default), 2 = one warp per block
-                               triple (tile <= 16) */
+                               triple (tile <= 16), 3 = one half-size CTA per
+                               block triple (tile >= 16) */
   double refine_at;         /* CC_PREC_FP32_REFINE: cc_solve leaves FP32 when
                                the violation is <= max(tol, refine_at) or stops
                                decreasing between checks; default 1e-5 */
+  int32_t trace;            /* 1: record per-work-item timestamps of each
+                               fused tiled sweep (cc_get_trace); default 0 */
+  int32_t interleave;       /* tiled schedule: 1 = deal the objects over the
+                               blocks (caller object i gets internal label
+                               lab(i): round r = 0..B-1 gives the next object
+                               to every block with more than r slots, blocks
+                               in order), so that consecutive objects fall in
+                               different blocks; the schedule is then the
+                               tiled order on the internal labels.  0 = blocks
+                               of consecutive objects.  Default 1.  Results
+                               are always exchanged in caller labels. */
 } cc_opts;
 
 typedef struct cc_stats {
@@ -167,6 +179,15 @@ int cc_refine_fp64(cc_handle* h);
  * nonnegative duals made consistent this way.  Tiled schedule, fused form,
  * FP64 state. */
 int cc_set_duals(cc_handle* h, const double* y_tri, const double* y_pair);
+
+/* Per-work-item timestamps of the most recent fused tiled sweep (opts.trace
+ * = 1): 6 uint64 per item in schedule order (block triples, then one pair
+ * item per tile): taken, dependencies met, processed, released (ns, GPU
+ * global timer; 0 where not applicable), unused, CTA index.  Copies
+ * min(cap, items) records into out (host); returns the number copied, the
+ * item count when out is NULL, 0 when tracing is off, -1 on a CUDA error.
+ * Synchronizes. */
+int64_t cc_get_trace(cc_handle* h, uint64_t* out, int64_t cap);
 
 /* Counters of the last check plus sweeps and last sweep time (no device work). */
 int cc_get_stats(cc_handle* h, cc_stats* st);

@@ -107,6 +107,25 @@ def workload(name: str):
         D = D + D.T
         Dp = D[np.ix_(perm, perm)]
         return n, Dp[iu, ju].copy(), w, "Chung-Lu n=1000 as chunglu1000 with node labels permuted (seed 7)"
+    if name == "chunglu1000deal":
+        n, B = 1000, 16
+        d, w, _ = chung_lu(n, 2.5, 8.0, seed=1)
+        nb = -(-n // B)
+        sizes = [min(B, n - b * B) for b in range(nb)]
+        label = np.empty(n, dtype=np.int64)     # original node -> new label, dealt round by round
+        i = 0
+        for r in range(B):
+            for b in range(nb):
+                if sizes[b] > r:
+                    label[i] = b * B + r
+                    i += 1
+        order = np.argsort(label)               # new label -> original node
+        D = np.zeros((n, n))
+        iu, ju = np.triu_indices(n, 1)
+        D[iu, ju] = d
+        D = D + D.T
+        Dp = D[np.ix_(order, order)]
+        return n, Dp[iu, ju].copy(), w, "Chung-Lu n=1000 relabeled by dealing nodes over 16-blocks"
     if name.startswith("chunglu") and name[7:].isdigit():
         n = int(name[7:])
         d, w, _ = chung_lu(n, 2.5, 8.0, seed=1)

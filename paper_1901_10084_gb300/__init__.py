@@ -70,7 +70,7 @@ class Solver:
     def __init__(self, n, d, w, eps=0.2, schedule="tiled", tile=16, precision="fp64",
                  exact=False, check_every=10, device=0, stream=None, torch_alloc=True,
                  barrier_timeout_s=2.0, grid=0, debug_skip_cta=-1, on_device=False, variant=0,
-                 refine_at=1e-5):
+                 refine_at=1e-5, trace=False, interleave=True):
         o = cc_opts_default()
         o.eps = float(eps)
         o.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
@@ -84,6 +84,8 @@ class Solver:
         o.debug_skip_cta = int(debug_skip_cta)
         o.variant = int(variant)
         o.refine_at = float(refine_at)
+        o.trace = 1 if trace else 0
+        o.interleave = 1 if interleave else 0
         self._alloc = None
         try:
             import torch
@@ -141,6 +143,9 @@ class Solver:
     def set_state(self, x, f, y_tri, y_pair) -> None:
         c = lambda a: np.ascontiguousarray(a, dtype=np.float64)
         cc_set_state(self.h, c(x), c(f), c(y_tri), c(y_pair))
+
+    def trace(self):
+        return _native.cc_get_trace(self.h)
 
     def refine_fp64(self) -> None:
         cc_refine_fp64(self.h)

@@ -49,6 +49,8 @@ class cc_opts(ctypes.Structure):
         ("debug_skip_cta", ctypes.c_int32),
         ("variant", ctypes.c_int32),
         ("refine_at", ctypes.c_double),
+        ("trace", ctypes.c_int32),
+        ("interleave", ctypes.c_int32),
     ]
 
 
@@ -74,7 +76,7 @@ class cc_stats(ctypes.Structure):
 EXPORTS = ("cc_opts_default", "cc_create", "cc_create_device", "cc_sweep", "cc_check",
            "cc_solve", "cc_get_x", "cc_get_duals", "cc_set_state", "cc_get_stats",
            "cc_device_bytes", "cc_destroy", "cc_last_error", "cc_check_noalloc",
-           "cc_refine_fp64", "cc_set_duals")
+           "cc_refine_fp64", "cc_set_duals", "cc_get_trace")
 
 _lib = None
 _lock = threading.Lock()
@@ -126,6 +128,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         lib.cc_destroy.restype = None
         lib.cc_last_error.argtypes = [H]
         lib.cc_last_error.restype = ctypes.c_char_p
+        lib.cc_get_trace.argtypes = [H, ctypes.POINTER(ctypes.c_uint64), i64]
+        lib.cc_get_trace.restype = i64
         lib.cc_refine_fp64.argtypes = [H]
         lib.cc_refine_fp64.restype = ctypes.c_int
         lib.cc_set_duals.argtypes = [H, dp, dp]
@@ -207,6 +211,19 @@ def cc_get_duals(h, y_tri, y_pair, tri_first: int = 0, tri_count: int = 0) -> No
 
 def cc_set_state(h, x, f, y_tri, y_pair) -> None:
     _check(load().cc_set_state(h, _dp(x), _dp(f), _dp(y_tri), _dp(y_pair)), h)
+
+
+def cc_get_trace(h):
+    """Per-item timestamps of the last fused tiled sweep as an (items, 6)
+    uint64 array (empty when tracing is off)."""
+    import numpy as np
+    items = int(load().cc_get_trace(h, None, 0))
+    out = np.zeros((max(items, 0), 6), dtype=np.uint64)
+    if items > 0:
+        got = load().cc_get_trace(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), items)
+        if got < 0:
+            raise CCError(CC_ERR_CUDA, "cc_get_trace failed")
+    return out
 
 
 def cc_refine_fp64(h) -> None:

@@ -56,6 +56,8 @@ struct cc_handle {
   uint32_t* mask = nullptr;  // nonzero-dual bits (fused form)
   int64_t mask_words = 0;
   int* flow = nullptr;       // dataflow sweep: item counter + visits per tile
+  unsigned long long* trace = nullptr;   // per-item timestamps of the last sweep (opts.trace)
+  int* lab = nullptr;        // caller label -> internal label (tiled schedule, opts.interleave)
   // schedules 0 and 1 (device tables)
   ListArgs la{};
   int* l_pre1 = nullptr;
@@ -152,8 +154,17 @@ void* sweep_kernel_b(int B) {
   }
 }
 
+int threads_for_tile(int B) { return B * B < 256 ? B * B : 256; }
+
 // warp-per-item kernel: warps per CTA
 int warps_per_cta(int B) { return B == 8 ? 8 : 4; }
+
+// CTA-per-item kernel: threads per CTA (variant 3: half of the default for
+// B >= 16, so that twice as many block triples are in flight per SM)
+int flow_threads(const cc_handle* h) {
+  const int full = threads_for_tile(h->B);
+  return (h->o.variant == 3 && h->B >= 16) ? full / 2 : full;
+}
 
 bool use_warp_kernel(const cc_handle* h) {
   if (h->o.exact || h->B > 16) return false;
@@ -161,12 +172,12 @@ bool use_warp_kernel(const cc_handle* h) {
 }
 
 template <typename T, bool UNITW>
-void* filtered_kernel_b(int B, bool warp) {
+void* filtered_kernel_b(int B, bool warp, bool half) {
   if (warp) return B == 8 ? (void*)k_sweep_warpflow<T, UNITW, 8> : (void*)k_sweep_warpflow<T, UNITW, 16>;
   switch (B) {
-    case 8: return (void*)k_sweep_flow<T, UNITW, 8>;
-    case 16: return (void*)k_sweep_flow<T, UNITW, 16>;
-    default: return (void*)k_sweep_flow<T, UNITW, 32>;
+    case 8: return (void*)k_sweep_flow<T, UNITW, 8, 64>;
+    case 16: return half ? (void*)k_sweep_flow<T, UNITW, 16, 128> : (void*)k_sweep_flow<T, UNITW, 16, 256>;
+    default: return half ? (void*)k_sweep_flow<T, UNITW, 32, 128> : (void*)k_sweep_flow<T, UNITW, 32, 256>;
   }
 }
 
@@ -190,11 +201,11 @@ void* sweep_kernel(cc_handle* h) {
   }
   if (h->o.exact) return h->unitw ? sweep_kernel_b<double, true, true>(h->B) : sweep_kernel_b<double, true, false>(h->B);
   const bool wk = use_warp_kernel(h);
-  if (h->fp32) return h->unitw ? filtered_kernel_b<float, true>(h->B, wk) : filtered_kernel_b<float, false>(h->B, wk);
-  return h->unitw ? filtered_kernel_b<double, true>(h->B, wk) : filtered_kernel_b<double, false>(h->B, wk);
+  const bool half = flow_threads(h) != threads_for_tile(h->B);
+  if (h->fp32) return h->unitw ? filtered_kernel_b<float, true>(h->B, wk, half) : filtered_kernel_b<float, false>(h->B, wk, half);
+  return h->unitw ? filtered_kernel_b<double, true>(h->B, wk, half) : filtered_kernel_b<double, false>(h->B, wk, half);
 }
 
-int threads_for_tile(int B) { return B * B < 256 ? B * B : 256; }
 
 template <typename T>
 TiledArgs<T> tiled_args(cc_handle* h) {
@@ -219,6 +230,7 @@ TiledArgs<T> tiled_args(cc_handle* h) {
   a.mask = h->mask;
   a.work = nullptr;
   a.nbt = h->nbt;
+  a.trace = h->trace;
   return a;
 }
 
@@ -237,7 +249,7 @@ int configure_sweep(cc_handle* h) {
     return CC_OK;
   }
   const bool wk = use_warp_kernel(h);
-  const int threads = wk ? 32 * warps_per_cta(h->B) : threads_for_tile(h->B);
+  const int threads = wk ? 32 * warps_per_cta(h->B) : flow_threads(h);
   h->dyn_smem = h->o.exact ? 0 : flow_smem(h->fp32, h->B) * (wk ? warps_per_cta(h->B) : 1);
   if (h->dyn_smem) CK(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->dyn_smem));
   int per_sm = 0;
@@ -342,6 +354,26 @@ int build_tables(cc_handle* h) {
   CK(h, cudaMemcpyAsync(h->bt_rank, rank.data(), rank.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
   CK(h, cudaMemcpyAsync(h->tile_list, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
   CK(h, cudaStreamSynchronize(h->st));  // host vectors go out of scope
+  return CC_OK;
+}
+
+// Relabeling of the tiled schedule: the objects are dealt over the blocks in
+// rounds (round r gives one object to every block with more than r slots),
+// so that objects that are close in the caller's order (e.g. sorted by
+// degree) land in different blocks and no tile collects all the activity of
+// a dense group.  Caller label i -> internal label lab[i].
+int build_labels(cc_handle* h) {
+  const int n = (int)h->n, B = h->B, nb = h->nb;
+  std::vector<int> lab(n);
+  int i = 0;
+  for (int r = 0; r < B; ++r)
+    for (int b = 0; b < nb; ++b)
+      if (std::min<int64_t>(B, h->n - (int64_t)b * B) > r) lab[i++] = b * B + r;
+  if (i != n) return fail(h, CC_ERR_ARG, "relabeling does not cover every object");
+  h->lab = (int*)dalloc(h, (size_t)n * sizeof(int));
+  if (!h->lab) return fail(h, CC_ERR_OOM, "relabeling");
+  CK(h, cudaMemcpyAsync(h->lab, lab.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
   return CC_OK;
 }
 
@@ -479,6 +511,9 @@ int create_common(cc_handle** out, int64_t n, const double* d_dev, const double*
     rc = build_list_tables(h);
     if (rc) return rc;
     h->zt_elems = 3 * h->T3;   // compact store in schedule order
+  } else if (h->o.interleave) {
+    rc = build_labels(h);
+    if (rc) return rc;
   }
   h->fp32 = h->o.precision == CC_PREC_FP32_REFINE;
   h->esz = h->fp32 ? 4 : 8;
@@ -501,6 +536,11 @@ int create_common(cc_handle** out, int64_t n, const double* d_dev, const double*
     h->mask_words = (int64_t)h->nbt * 3 * h->B * ((h->B * h->B) / 32);
     h->mask = (uint32_t*)dalloc(h, (size_t)h->mask_words * sizeof(uint32_t));
     h->flow = (int*)dalloc(h, (size_t)(1 + h->ntiles) * sizeof(int));
+    if (h->o.trace) {
+      h->trace = (unsigned long long*)dalloc(h, (size_t)(h->nbt + h->ntiles) * 6 * sizeof(unsigned long long));
+      if (!h->trace) return fail(h, CC_ERR_OOM, "trace buffer");
+      CK(h, cudaMemsetAsync(h->trace, 0, (size_t)(h->nbt + h->ntiles) * 6 * sizeof(unsigned long long), h->st));
+    }
     if (!h->mask || !h->flow) return fail(h, CC_ERR_OOM, "dual bitmask");
     CK(h, cudaMemsetAsync(h->mask, 0, (size_t)h->mask_words * sizeof(uint32_t), h->st));
   }
@@ -513,7 +553,7 @@ int create_common(cc_handle** out, int64_t n, const double* d_dev, const double*
   CK(h, cudaMemsetAsync(h->d64, 0, te * sizeof(double), h->st));
   k_fill<double><<<grid_for(h, te, 256), 256, 0, h->st>>>(h->winv64, te, 1.0);
   k_load_problem<double><<<grid_for(h, h->P, 256), 256, 0, h->st>>>(d_dev, w_dev, (int)n, h->nb, h->B, h->d64,
-                                                                     h->winv64);
+                                                                     h->winv64, h->lab);
   if (h->fp32) {
     k_convert<double, float><<<grid_for(h, te, 256), 256, 0, h->st>>>(h->d64, (float*)h->d, te);
     k_convert<double, float><<<grid_for(h, te, 256), 256, 0, h->st>>>(h->winv64, (float*)h->winv, te);
@@ -655,6 +695,8 @@ void cc_opts_default(cc_opts* o) {
   o->debug_skip_cta = -1;
   o->variant = 0;
   o->refine_at = 1e-5;
+  o->trace = 0;
+  o->interleave = 1;
 }
 
 int cc_create_device(cc_handle** out, int64_t n, const double* d_dev, const double* w_dev, const cc_opts* opts) {
@@ -828,9 +870,9 @@ int cc_get_x(cc_handle* h, double* x, double* f) {
   double* sf = h->stage + h->P;
   const int g = grid_for(h, h->P, 256);
   if (h->fp32)
-    k_pairs_layout<float><<<g, 256, 0, h->st>>>((float*)h->x, (float*)h->f, (int)h->n, h->nb, h->B, sx, sf, 0);
+    k_pairs_layout<float><<<g, 256, 0, h->st>>>((float*)h->x, (float*)h->f, (int)h->n, h->nb, h->B, sx, sf, 0, h->lab);
   else
-    k_pairs_layout<double><<<g, 256, 0, h->st>>>((double*)h->x, (double*)h->f, (int)h->n, h->nb, h->B, sx, sf, 0);
+    k_pairs_layout<double><<<g, 256, 0, h->st>>>((double*)h->x, (double*)h->f, (int)h->n, h->nb, h->B, sx, sf, 0, h->lab);
   CK(h, cudaGetLastError());
   if (x) CK(h, cudaMemcpyAsync(x, sx, h->P * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   if (f) CK(h, cudaMemcpyAsync(f, sf, h->P * sizeof(double), cudaMemcpyDeviceToHost, h->st));
@@ -861,7 +903,7 @@ static int move_duals(cc_handle* h, double* y_tri, double* y_pair, int64_t first
         continue;
       }
 #define LAUNCH_TD(T, BV) \
-  k_tri_duals_tiled<T, BV><<<g, 256, 0, h->st>>>((T*)h->zt, h->bt_rank, (int)h->n, h->nb, first + c0, m, h->stage, scale, dir);
+  k_tri_duals_tiled<T, BV><<<g, 256, 0, h->st>>>((T*)h->zt, h->bt_rank, (int)h->n, h->nb, first + c0, m, h->stage, scale, dir, h->lab);
       if (h->fp32) {
         if (h->B == 8) { LAUNCH_TD(float, 8) } else if (h->B == 16) { LAUNCH_TD(float, 16) } else { LAUNCH_TD(float, 32) }
       } else {
@@ -879,9 +921,9 @@ static int move_duals(cc_handle* h, double* y_tri, double* y_pair, int64_t first
       CK(h, cudaMemcpyAsync(h->stage, y_pair, 2 * h->P * sizeof(double), cudaMemcpyHostToDevice, h->st));
     const int g = grid_for(h, h->P, 256);
     if (h->fp32)
-      k_pair_duals_tiled<float><<<g, 256, 0, h->st>>>((float*)h->zp, (int)h->n, h->nb, h->B, h->stage, scale, dir);
+      k_pair_duals_tiled<float><<<g, 256, 0, h->st>>>((float*)h->zp, (int)h->n, h->nb, h->B, h->stage, scale, dir, h->lab);
     else
-      k_pair_duals_tiled<double><<<g, 256, 0, h->st>>>((double*)h->zp, (int)h->n, h->nb, h->B, h->stage, scale, dir);
+      k_pair_duals_tiled<double><<<g, 256, 0, h->st>>>((double*)h->zp, (int)h->n, h->nb, h->B, h->stage, scale, dir, h->lab);
     CK(h, cudaGetLastError());
     if (dir == 0)
       CK(h, cudaMemcpyAsync(y_pair, h->stage, 2 * h->P * sizeof(double), cudaMemcpyDeviceToHost, h->st));
@@ -913,10 +955,10 @@ int cc_set_state(cc_handle* h, const double* x, const double* f, const double* y
   const int g = grid_for(h, h->P, 256);
   if (h->fp32)
     k_pairs_layout<float><<<g, 256, 0, h->st>>>((float*)h->x, (float*)h->f, (int)h->n, h->nb, h->B, h->stage,
-                                                h->stage + h->P, 1);
+                                                h->stage + h->P, 1, h->lab);
   else
     k_pairs_layout<double><<<g, 256, 0, h->st>>>((double*)h->x, (double*)h->f, (int)h->n, h->nb, h->B, h->stage,
-                                                 h->stage + h->P, 1);
+                                                 h->stage + h->P, 1, h->lab);
   CK(h, cudaGetLastError());
   CK(h, cudaStreamSynchronize(h->st));
   rc = move_duals(h, const_cast<double*>(y_tri), const_cast<double*>(y_pair), 0, h->T3, 1);
@@ -963,6 +1005,17 @@ int cc_set_duals(cc_handle* h, const double* y_tri, const double* y_pair) {
   h->sweeps = 0;
   h->fp32_sweeps = 0;
   return CC_OK;
+}
+
+int64_t cc_get_trace(cc_handle* h, uint64_t* out, int64_t cap) {
+  if (!h || !h->trace) return 0;
+  const int64_t items = (int64_t)h->nbt + h->ntiles;
+  if (!out) return items;
+  const int64_t m = std::min(cap, items);
+  if (cudaMemcpyAsync(out, h->trace, (size_t)m * 6 * sizeof(uint64_t), cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
+      cudaStreamSynchronize(h->st) != cudaSuccess)
+    return -1;
+  return m;
 }
 
 int cc_get_stats(cc_handle* h, cc_stats* st) {

@@ -50,6 +50,7 @@ struct TiledArgs {
   uint32_t* mask;       // nonzero-dual bits, same schedule order as zt (filtered form)
   int* work;            // unused
   int nbt;              // block triples per sweep
+  unsigned long long* trace;  // optional per-item timestamps (nullptr = off)
 };
 
 __device__ __forceinline__ void unpack_bt(int pk, int& I, int& J, int& K) {
@@ -191,22 +192,19 @@ __global__ void __launch_bounds__(TileCfg<B>::NT) k_sweep_tiled(TiledArgs<T> a) 
 // sweep's in value.  Warps whose 32 triplets are all inactive skip the FP64
 // work entirely (a warp vote).
 
-__device__ __forceinline__ bool row_inactive_f(float h, float a, float b) {
-  const float dl = (h - a) - b;
-  const float S = fabsf(h) + fabsf(a) + fabsf(b);
-  return dl <= -fmaf(S, 0x1p-21f, 0x1p-100f);
-}
-
-template <typename T>
-__device__ __forceinline__ bool triplet_inactive(T xij, T xik, T xjk);
-
-template <>
-__device__ __forceinline__ bool triplet_inactive<float>(float xij, float xik, float xjk) {
-  return ((xij - xik) - xjk) <= 0.0f && ((xik - xij) - xjk) <= 0.0f && ((xjk - xij) - xik) <= 0.0f;
-}
-
-__device__ __forceinline__ bool triplet_inactive_shadow(float fij, float fik, float fjk) {
-  return row_inactive_f(fij, fik, fjk) && row_inactive_f(fik, fij, fjk) && row_inactive_f(fjk, fij, fik);
+// All three rows of a triplet proved satisfied from float values.  The
+// largest row delta is 2 max(x) - sum(x); evaluated in float from values
+// rounded to nearest (or exact, for FP32 state) it is within 8 * 2^-24 * S =
+// 2^-21 S of the exact one (S = |x_ij| + |x_ik| + |x_jk|; three conversions,
+// two additions and one fused multiply-add, each rounded to nearest), so
+// dmax <= -(2^-20 S + 2^-100) proves every row delta < 0 with a margin far
+// above the rounding of the double (or float) row evaluation itself.
+__device__ __forceinline__ bool inactive_fast(float a, float b, float c) {
+  const float sum = (a + b) + c;
+  const float mx = fmaxf(fmaxf(a, b), c);
+  const float dmax = fmaf(2.0f, mx, -sum);
+  const float S = (fabsf(a) + fabsf(b)) + fabsf(c);
+  return dmax <= -fmaf(S, 0x1p-20f, 0x1p-100f);
 }
 
 template <int B>
@@ -244,31 +242,52 @@ struct alignas(16) FlowSmem {
   uint32_t mask[MaskCfg<B>::PER_BT];
   int pre[MaskCfg<B>::PER_BT];
   T dual[MaskCfg<B>::CAP];
+  T lz[3][BB];              // compacted list of a sub-phase: current duals
+  int lslot[BB];            //   and slots of the triplets to update
+  int lcnt[B];              // list length per sub-phase
   int scan[32];
-  int item, flag, total;
+  int item, flag, total, dirty;
 };
 
-// Wait (thread 0) until each listed tile has been visited `need` times.
+__device__ __forceinline__ int ld_relaxed_i32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Wait (thread 0) until each listed tile has been visited `need` times: the
+// (up to three) counters are polled together with relaxed loads, then an
+// acquire fence orders the item's reads after the visits it waited for.
 // Bounded in time; on expiry records CC_ERR_TIMEOUT.  Returns false when the
 // kernel must stop.
 __device__ __forceinline__ bool wait_tiles(const int* cnt, int64_t t0, int64_t t1, int64_t t2, int need,
                                            Ctl* ctl, long long timeout_ns, int tag) {
-  const int64_t ts[3] = {t0, t1, t2};
   unsigned long long start = 0;
   unsigned spins = 0;
-  for (int q = 0; q < 3; ++q) {
-    if (ts[q] < 0) continue;
-    while (ld_acquire_s32(cnt + ts[q]) < need) {
-      if (ld_relaxed_s32(&ctl->err) != 0) return false;
-      if (start == 0) start = global_ns();
-      if ((++spins & 15u) == 0 && (long long)(global_ns() - start) > timeout_ns) {
-        if (atomicCAS(&ctl->err, 0, CC_ERR_TIMEOUT) == 0) ctl->err_phase = tag;
-        return false;
-      }
-      __nanosleep(128);
+  while (true) {
+    const int c0 = ld_relaxed_i32(cnt + t0);
+    const int c1 = t1 >= 0 ? ld_relaxed_i32(cnt + t1) : need;
+    const int c2 = t2 >= 0 ? ld_relaxed_i32(cnt + t2) : need;
+    if (c0 >= need && c1 >= need && c2 >= need) break;
+    if (ld_relaxed_s32(&ctl->err) != 0) return false;
+    if (start == 0) start = global_ns();
+    if ((++spins & 15u) == 0 && (long long)(global_ns() - start) > timeout_ns) {
+      if (atomicCAS(&ctl->err, 0, CC_ERR_TIMEOUT) == 0) ctl->err_phase = tag;
+      return false;
     }
+    if (spins > 4) __nanosleep(64);
   }
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
   return true;
+}
+
+// Release (thread 0, after a CTA barrier): make the item's writes visible at
+// GPU scope, then count one visit on each of its tiles.
+__device__ __forceinline__ void release_tiles(int* cnt, int64_t t0, int64_t t1, int64_t t2) {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  atomicAdd(cnt + t0, 1);
+  if (t1 >= 0) atomicAdd(cnt + t1, 1);
+  if (t2 >= 0) atomicAdd(cnt + t2, 1);
 }
 
 template <bool WARP>
@@ -277,17 +296,246 @@ __device__ __forceinline__ void item_sync() {
   else __syncthreads();
 }
 
+// The B sub-phases of one staged block triple.  FULL: I < J < K and no
+// ragged block, so every slot is a triplet and the thread owns its x_ij
+// (tile (I,J) entry (a,b) is touched only by slot (a,b)): x_ij and its float
+// value stay in registers for the whole item.  HASMASK = false: the item has
+// no nonzero dual, so no mask word is read.  Returns whether this thread
+// updated anything.
+template <typename T, bool UNITW, int B, int NTH_, bool FULL, bool HASMASK>
+__device__ __forceinline__ int flow_subphases(const TiledArgs<T>& a, int w, FlowSmem<T, B>& sm, T* pIJ, T* pIK,
+                                              T* pJK, float* gIJ, float* gIK, float* gJK, int64_t oIJ,
+                                              int64_t oIK, int64_t oJK, bool ij, bool kj, int kB, bool staged,
+                                              int tid, int lane, T* zb) {
+  using C = TileCfg<B>;
+  using M = MaskCfg<B>;
+  constexpr bool SHADOW = sizeof(T) == 8;
+  constexpr bool WARP = NTH_ == 32;
+  constexpr int NTH = NTH_;
+  constexpr int SPT = C::BB / NTH;
+  const uint32_t below = (1u << lane) - 1u;
+  int la[SPT], lb[SPT];
+  T xr[SPT];
+  float fr[SPT];
+#pragma unroll
+  for (int q = 0; q < SPT; ++q) {
+    const int slot = tid + q * NTH;
+    la[q] = slot / B;
+    lb[q] = slot % B;
+    if constexpr (FULL) {
+      xr[q] = pIJ[slot];
+      fr[q] = gIJ[slot];
+    }
+  }
+  int touched = 0;
+  for (int t = 0; t < B; ++t) {
+    T* zs = zb + (int64_t)t * (3 * C::BB);
+    const int qt = t * (3 * M::WPR);
+#pragma unroll
+    for (int q = 0; q < SPT; ++q) {
+      const int slot = tid + q * NTH;
+      const int lc = (t - la[q] - lb[q]) & (B - 1);
+      const int eij = slot, eik = la[q] * B + lc, ejk = lb[q] * B + lc;
+      bool valid = true;
+      if constexpr (!FULL) valid = (!ij || la[q] < lb[q]) && (!kj || lb[q] < lc) && (kB + lc < a.n);
+      const int wd = slot >> 5;
+      const int q0 = qt + wd, q1 = qt + M::WPR + wd, q2 = qt + 2 * M::WPR + wd;
+      uint32_t m0 = 0u, m1 = 0u, m2 = 0u;
+      if constexpr (HASMASK) {
+        m0 = sm.mask[q0];
+        m1 = sm.mask[q1];
+        m2 = sm.mask[q2];
+      }
+      const bool b0 = (m0 >> lane) & 1u, b1 = (m1 >> lane) & 1u, b2 = (m2 >> lane) & 1u;
+      bool need = false;
+      if (valid) {
+        const float fij = FULL ? fr[q] : gIJ[eij];
+        need = (b0 | b1 | b2) || !inactive_fast(fij, gIK[eik], gJK[ejk]);
+      }
+      if (__any_sync(0xffffffffu, need)) {
+        T z0 = T(0), z1 = T(0), z2 = T(0);
+        if (need) {
+          if (staged) {
+            if (b0) z0 = sm.dual[sm.pre[q0] + __popc(m0 & below)];
+            if (b1) z1 = sm.dual[sm.pre[q1] + __popc(m1 & below)];
+            if (b2) z2 = sm.dual[sm.pre[q2] + __popc(m2 & below)];
+          } else {
+            if (b0) z0 = ld_stream(zs + slot);
+            if (b1) z1 = ld_stream(zs + C::BB + slot);
+            if (b2) z2 = ld_stream(zs + 2 * C::BB + slot);
+          }
+          const T o0 = z0, o1 = z1, o2 = z2;
+          T xij = FULL ? xr[q] : pIJ[eij];
+          T xik = pIK[eik], xjk = pJK[ejk];
+          T vij = T(1), vik = T(1), vjk = T(1);
+          if (!UNITW) {
+            vij = a.winv[oIJ + eij];
+            vik = a.winv[oIK + eik];
+            vjk = a.winv[oJK + ejk];
+          }
+          triplet_rows<T, false, UNITW>(xij, xik, xjk, vij, vik, vjk, a.eps, a.r_unit, z0, z1, z2);
+          if constexpr (FULL) {
+            xr[q] = xij;
+            fr[q] = (float)xij;
+          } else {
+            pIJ[eij] = xij;
+            if constexpr (SHADOW) gIJ[eij] = (float)xij;
+          }
+          pIK[eik] = xik;
+          pJK[ejk] = xjk;
+          if constexpr (SHADOW) {
+            gIK[eik] = (float)xik;
+            gJK[ejk] = (float)xjk;
+          }
+          if (z0 != o0) st_stream(zs + slot, z0);
+          if (z1 != o1) st_stream(zs + C::BB + slot, z1);
+          if (z2 != o2) st_stream(zs + 2 * C::BB + slot, z2);
+          touched = 1;
+        }
+        const uint32_t n0 = __ballot_sync(0xffffffffu, need ? (z0 != T(0)) : b0);
+        const uint32_t n1 = __ballot_sync(0xffffffffu, need ? (z1 != T(0)) : b1);
+        const uint32_t n2 = __ballot_sync(0xffffffffu, need ? (z2 != T(0)) : b2);
+        if (lane == 0) {
+          uint32_t* mw = a.mask + (int64_t)w * M::PER_BT;
+          if (n0 != m0) mw[q0] = n0;
+          if (n1 != m1) mw[q1] = n1;
+          if (n2 != m2) mw[q2] = n2;
+        }
+      }
+    }
+    item_sync<WARP>();
+  }
+  if constexpr (FULL) {
+#pragma unroll
+    for (int q = 0; q < SPT; ++q) pIJ[tid + q * NTH] = xr[q];
+  }
+  return touched;
+}
+
+// The B sub-phases with compaction (CTA per item).  A filter pass lists, in
+// shared memory, the triplets of the sub-phase that need the update together
+// with their current duals; the first threads of the CTA then process the
+// list, so the FP64 work of a sub-phase occupies as few warps as possible
+// (the triplets of a sub-phase are independent, so which thread handles which
+// triplet does not change the result).  Mask bits are updated in shared
+// memory and written back once per item.  FULL / HASMASK as above.
+template <typename T, bool UNITW, int B, int NTH_, bool FULL, bool HASMASK>
+__device__ __forceinline__ int flow_subphases_compact(const TiledArgs<T>& a, FlowSmem<T, B>& sm, T* pIJ, T* pIK,
+                                                      T* pJK, float* gIJ, float* gIK, float* gJK, int64_t oIJ,
+                                                      int64_t oIK, int64_t oJK, bool ij, bool kj, int kB,
+                                                      bool staged, int tid, int lane, T* zb) {
+  using C = TileCfg<B>;
+  using M = MaskCfg<B>;
+  constexpr bool SHADOW = sizeof(T) == 8;
+  constexpr bool WARP = NTH_ == 32;
+  constexpr int NTH = NTH_;
+  constexpr int SPT = C::BB / NTH;
+  const uint32_t below = (1u << lane) - 1u;
+  int touched = 0;
+  for (int t = 0; t < B; ++t) {
+    T* zs = zb + (int64_t)t * (3 * C::BB);
+    const int qt = t * (3 * M::WPR);
+#pragma unroll
+    for (int q = 0; q < SPT; ++q) {
+      const int slot = tid + q * NTH;
+      const int la = slot / B, lb = slot % B, lc = (t - la - lb) & (B - 1);
+      bool valid = true;
+      if constexpr (!FULL) valid = (!ij || la < lb) && (!kj || lb < lc) && (kB + lc < a.n);
+      const int wd = slot >> 5;
+      const int q0 = qt + wd, q1 = qt + M::WPR + wd, q2 = qt + 2 * M::WPR + wd;
+      uint32_t m0 = 0u, m1 = 0u, m2 = 0u;
+      if constexpr (HASMASK) {
+        m0 = sm.mask[q0];
+        m1 = sm.mask[q1];
+        m2 = sm.mask[q2];
+      }
+      const bool b0 = (m0 >> lane) & 1u, b1 = (m1 >> lane) & 1u, b2 = (m2 >> lane) & 1u;
+      if (valid && ((b0 | b1 | b2) || !inactive_fast(gIJ[slot], gIK[la * B + lc], gJK[lb * B + lc]))) {
+        T z0 = T(0), z1 = T(0), z2 = T(0);
+        if (staged) {
+          if (b0) z0 = sm.dual[sm.pre[q0] + __popc(m0 & below)];
+          if (b1) z1 = sm.dual[sm.pre[q1] + __popc(m1 & below)];
+          if (b2) z2 = sm.dual[sm.pre[q2] + __popc(m2 & below)];
+        } else {
+          if (b0) z0 = ld_stream(zs + slot);
+          if (b1) z1 = ld_stream(zs + C::BB + slot);
+          if (b2) z2 = ld_stream(zs + 2 * C::BB + slot);
+        }
+        const int pos = atomicAdd(&sm.lcnt[t], 1);
+        sm.lslot[pos] = slot;
+        sm.lz[0][pos] = z0;
+        sm.lz[1][pos] = z1;
+        sm.lz[2][pos] = z2;
+      }
+    }
+    item_sync<WARP>();
+    const int cnt = sm.lcnt[t];
+    if (cnt > 0) {
+      for (int p = tid; p < cnt; p += NTH) {
+        const int slot = sm.lslot[p];
+        const int la = slot / B, lb = slot % B, lc = (t - la - lb) & (B - 1);
+        const int eij = slot, eik = la * B + lc, ejk = lb * B + lc;
+        T z0 = sm.lz[0][p], z1 = sm.lz[1][p], z2 = sm.lz[2][p];
+        const T o0 = z0, o1 = z1, o2 = z2;
+        T xij = pIJ[eij], xik = pIK[eik], xjk = pJK[ejk];
+        T vij = T(1), vik = T(1), vjk = T(1);
+        if (!UNITW) {
+          vij = a.winv[oIJ + eij];
+          vik = a.winv[oIK + eik];
+          vjk = a.winv[oJK + ejk];
+        }
+        triplet_rows<T, false, UNITW>(xij, xik, xjk, vij, vik, vjk, a.eps, a.r_unit, z0, z1, z2);
+        pIJ[eij] = xij;
+        pIK[eik] = xik;
+        pJK[ejk] = xjk;
+        if constexpr (SHADOW) {
+          gIJ[eij] = (float)xij;
+          gIK[eik] = (float)xik;
+          gJK[ejk] = (float)xjk;
+        }
+        const uint32_t bit = 1u << (slot & 31);
+        const int wq = qt + (slot >> 5);
+        if (z0 != o0) {
+          st_stream(zs + slot, z0);
+          if ((z0 != T(0)) != (o0 != T(0))) {
+            if (z0 != T(0)) atomicOr(&sm.mask[wq], bit); else atomicAnd(&sm.mask[wq], ~bit);
+            sm.dirty = 1;
+          }
+        }
+        if (z1 != o1) {
+          st_stream(zs + C::BB + slot, z1);
+          if ((z1 != T(0)) != (o1 != T(0))) {
+            if (z1 != T(0)) atomicOr(&sm.mask[wq + M::WPR], bit); else atomicAnd(&sm.mask[wq + M::WPR], ~bit);
+            sm.dirty = 1;
+          }
+        }
+        if (z2 != o2) {
+          st_stream(zs + 2 * C::BB + slot, z2);
+          if ((z2 != T(0)) != (o2 != T(0))) {
+            if (z2 != T(0)) atomicOr(&sm.mask[wq + 2 * M::WPR], bit); else atomicAnd(&sm.mask[wq + 2 * M::WPR], ~bit);
+            sm.dirty = 1;
+          }
+        }
+        touched = 1;
+      }
+      item_sync<WARP>();
+    }
+  }
+  return touched;
+}
+
 // One block triple, processed by one CTA (WARP = false) or by one warp alone
 // (WARP = true): stage tiles, mask and nonzero duals in shared memory
 // (asynchronous copies, one round of memory latency per item), then walk
 // the B sub-phases.
-template <typename T, bool UNITW, int B, bool WARP>
+template <typename T, bool UNITW, int B, int NTH_>
 __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, int I, int J, int K,
                                                   FlowSmem<T, B>& sm) {
   using C = TileCfg<B>;
   using M = MaskCfg<B>;
   constexpr bool SHADOW = sizeof(T) == 8;
-  constexpr int NTH = WARP ? 32 : C::NT;         // threads working on the item
+  constexpr bool WARP = NTH_ == 32;
+  constexpr int NTH = NTH_;                      // threads working on the item
   constexpr int SPT = C::BB / NTH;               // slots per thread and sub-phase
   constexpr int NW = NTH / 32;
   const int tid = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -298,9 +546,20 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
   T* pIJ = sm.x[0];
   T* pIK = kj ? sm.x[0] : sm.x[1];
   T* pJK = ij ? pIK : sm.x[2];
-  float* gIJ = sm.f[0];
-  float* gIK = SHADOW ? (kj ? sm.f[0] : sm.f[SHADOW ? 1 : 0]) : sm.f[0];
-  float* gJK = SHADOW ? (ij ? gIK : sm.f[SHADOW ? 2 : 0]) : sm.f[0];
+  // float values the pre-filter reads: a float copy of FP64 tiles, the
+  // tiles themselves for FP32 state
+  float* gIJ;
+  float* gIK;
+  float* gJK;
+  if constexpr (SHADOW) {
+    gIJ = sm.f[0];
+    gIK = kj ? sm.f[0] : sm.f[SHADOW ? 1 : 0];
+    gJK = ij ? gIK : sm.f[SHADOW ? 2 : 0];
+  } else {
+    gIJ = reinterpret_cast<float*>(pIJ);
+    gIK = reinterpret_cast<float*>(pIK);
+    gJK = reinterpret_cast<float*>(pJK);
+  }
   T* zb = a.zt + (int64_t)w * (3 * B * C::BB);
   const uint32_t* mb = a.mask + (int64_t)w * M::PER_BT;
 
@@ -314,6 +573,8 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
   constexpr int MCH = M::PER_BT * 4 / 16;
   for (int e = tid; e < MCH; e += NTH)
     cp_async16(reinterpret_cast<char*>(sm.mask) + 16 * e, reinterpret_cast<const char*>(mb) + 16 * e);
+  for (int e = tid; e < B; e += NTH) sm.lcnt[e] = 0;
+  if (tid == 0) sm.dirty = 0;
   cp_async_wait_all();
   item_sync<WARP>();
 
@@ -345,6 +606,7 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
   item_sync<WARP>();
   int run = (wid ? sm.scan[wid - 1] : 0) + incl - cnt;
   const int total = sm.scan[NW - 1];
+  if (tid == 0) sm.total = total;
   const bool staged = total <= M::CAP;
 #pragma unroll
   for (int c = 0; c < CH; ++c) {
@@ -376,80 +638,40 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
   item_sync<WARP>();
 
   const int kB = K * B;
-  int touched = 0;
-  for (int t = 0; t < B; ++t) {
-    T* zs = zb + (int64_t)t * (3 * C::BB);
-    const int qt = t * (3 * M::WPR);
-    for (int q = 0; q < SPT; ++q) {
-      const int slot = tid + q * NTH;
-      const int la = slot / B, lb = slot % B;
-      const int lc = (t - la - lb) & (B - 1);
-      const bool valid = (!ij || la < lb) && (!kj || lb < lc) && (kB + lc < a.n);
-      const int wd = slot >> 5;
-      const int q0 = qt + wd, q1 = qt + M::WPR + wd, q2 = qt + 2 * M::WPR + wd;
-      const uint32_t m0 = sm.mask[q0], m1 = sm.mask[q1], m2 = sm.mask[q2];
-      const uint32_t below = (1u << lane) - 1u;
-      const bool b0 = (m0 >> lane) & 1u, b1 = (m1 >> lane) & 1u, b2 = (m2 >> lane) & 1u;
-      const int eij = la * B + lb, eik = la * B + lc, ejk = lb * B + lc;
-      bool need = false;
-      if (valid) {
-        if (b0 | b1 | b2) {
-          need = true;
-        } else {
-          if constexpr (SHADOW) need = !triplet_inactive_shadow(gIJ[eij], gIK[eik], gJK[ejk]);
-          else need = !triplet_inactive<T>(pIJ[eij], pIK[eik], pJK[ejk]);
-        }
-      }
-      if (__any_sync(0xffffffffu, need)) {
-        T z0 = T(0), z1 = T(0), z2 = T(0);
-        if (need) {
-          if (staged) {
-            if (b0) z0 = sm.dual[sm.pre[q0] + __popc(m0 & below)];
-            if (b1) z1 = sm.dual[sm.pre[q1] + __popc(m1 & below)];
-            if (b2) z2 = sm.dual[sm.pre[q2] + __popc(m2 & below)];
-          } else {
-            if (b0) z0 = ld_stream(zs + slot);
-            if (b1) z1 = ld_stream(zs + C::BB + slot);
-            if (b2) z2 = ld_stream(zs + 2 * C::BB + slot);
-          }
-          const T o0 = z0, o1 = z1, o2 = z2;
-          T xij = pIJ[eij], xik = pIK[eik], xjk = pJK[ejk];
-          T vij = T(1), vik = T(1), vjk = T(1);
-          if (!UNITW) {
-            vij = a.winv[oIJ + eij];
-            vik = a.winv[oIK + eik];
-            vjk = a.winv[oJK + ejk];
-          }
-          triplet_rows<T, false, UNITW>(xij, xik, xjk, vij, vik, vjk, a.eps, a.r_unit, z0, z1, z2);
-          pIJ[eij] = xij;
-          pIK[eik] = xik;
-          pJK[ejk] = xjk;
-          if constexpr (SHADOW) {
-            gIJ[eij] = (float)xij;
-            gIK[eik] = (float)xik;
-            gJK[ejk] = (float)xjk;
-          }
-          if (z0 != o0) st_stream(zs + slot, z0);
-          if (z1 != o1) st_stream(zs + C::BB + slot, z1);
-          if (z2 != o2) st_stream(zs + 2 * C::BB + slot, z2);
-          touched = 1;
-        }
-        const uint32_t n0 = __ballot_sync(0xffffffffu, need ? (z0 != T(0)) : b0);
-        const uint32_t n1 = __ballot_sync(0xffffffffu, need ? (z1 != T(0)) : b1);
-        const uint32_t n2 = __ballot_sync(0xffffffffu, need ? (z2 != T(0)) : b2);
-        if (lane == 0) {
-          uint32_t* mw = a.mask + (int64_t)w * M::PER_BT;
-          if (n0 != m0) mw[q0] = n0;
-          if (n1 != m1) mw[q1] = n1;
-          if (n2 != m2) mw[q2] = n2;
-        }
-      }
-    }
-    item_sync<WARP>();
+  const bool full = (I < J) && (J < K) && (kB + B <= a.n);
+  int touched;
+  // compaction pays for FP64 updates (few warps on the slow FP64 pipe); the
+  // FP32 update is cheap enough that the plain per-warp path is faster
+  if constexpr (WARP || !SHADOW) {
+    if (full && total == 0)
+      touched = flow_subphases<T, UNITW, B, NTH_, true, false>(a, w, sm, pIJ, pIK, pJK, gIJ, gIK, gJK, oIJ, oIK,
+                                                               oJK, false, false, kB, staged, tid, lane, zb);
+    else if (full)
+      touched = flow_subphases<T, UNITW, B, NTH_, true, true>(a, w, sm, pIJ, pIK, pJK, gIJ, gIK, gJK, oIJ, oIK,
+                                                              oJK, false, false, kB, staged, tid, lane, zb);
+    else
+      touched = flow_subphases<T, UNITW, B, NTH_, false, true>(a, w, sm, pIJ, pIK, pJK, gIJ, gIK, gJK, oIJ, oIK,
+                                                               oJK, ij, kj, kB, staged, tid, lane, zb);
+  } else {
+    if (full && total == 0)
+      touched = flow_subphases_compact<T, UNITW, B, NTH_, true, false>(a, sm, pIJ, pIK, pJK, gIJ, gIK, gJK, oIJ,
+                                                                       oIK, oJK, false, false, kB, staged, tid,
+                                                                       lane, zb);
+    else if (full)
+      touched = flow_subphases_compact<T, UNITW, B, NTH_, true, true>(a, sm, pIJ, pIK, pJK, gIJ, gIK, gJK, oIJ, oIK,
+                                                                      oJK, false, false, kB, staged, tid, lane, zb);
+    else
+      touched = flow_subphases_compact<T, UNITW, B, NTH_, false, true>(a, sm, pIJ, pIK, pJK, gIJ, gIK, gJK, oIJ,
+                                                                       oIK, oJK, ij, kj, kB, staged, tid, lane,
+                                                                       zb);
   }
   bool any_touched;
   if constexpr (WARP) any_touched = __any_sync(0xffffffffu, touched);
   else any_touched = __syncthreads_or(touched);
+  if (!WARP && SHADOW && sm.dirty) {
+    uint32_t* mw = a.mask + (int64_t)w * M::PER_BT;
+    for (int e = tid; e < M::PER_BT; e += NTH) mw[e] = sm.mask[e];
+  }
   if (any_touched) {
     for (int e = tid; e < C::BB; e += NTH) {
       a.x[oIJ + e] = sm.x[0][e];
@@ -461,10 +683,11 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
 }
 
 // The pair rows of one tile (a pair item of the dataflow sweep).
-template <typename T, int B, bool WARP>
+template <typename T, int B, int NTH_>
 __device__ __forceinline__ void flow_pair_tile(const TiledArgs<T>& a, int tl) {
   using C = TileCfg<B>;
-  constexpr int NTH = WARP ? 32 : C::NT;
+  constexpr bool WARP = NTH_ == 32;
+  constexpr int NTH = NTH_;
   const int tid = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
   const int pk = a.tile_list[tl];
   const int I = pk & 0xffff, J = pk >> 16;
@@ -491,20 +714,25 @@ __device__ __forceinline__ void flow_pair_tile(const TiledArgs<T>& a, int tl) {
 // tiles has g visits (counters in `tile_cnt`), and a tile's pair item once it
 // has Nb.  No grid-wide barrier: a CTA waits only for the items it depends
 // on, which were taken earlier by resident CTAs.
-template <typename T, bool UNITW, int B>
-__global__ void __launch_bounds__(TileCfg<B>::NT) k_sweep_flow(TiledArgs<T> a, int* flow) {
+template <typename T, bool UNITW, int B, int NT>
+__global__ void __launch_bounds__(NT) k_sweep_flow(TiledArgs<T> a, int* flow) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FlowSmem<T, B>& sm = *reinterpret_cast<FlowSmem<T, B>*>(smem_raw);
   int* const next = flow;            // item counter
   int* const tile_cnt = flow + 1;    // visits per tile in this sweep
   const int total = a.nbt + a.ntiles;
   bool first = true;
-  while (true) {
-    if (threadIdx.x == 0) sm.item = atomicAdd(next, 1);
-    __syncthreads();
-    const int w = sm.item;
-    __syncthreads();
-    if (w >= total) break;
+  if (threadIdx.x == 0) sm.item = atomicAdd(next, 1);
+  __syncthreads();
+  int w = sm.item;
+  while (w < total) {
+    int nxt = 0;
+    if (threadIdx.x == 0) nxt = atomicAdd(next, 1);   // the following item, fetched while this one runs
+    unsigned long long* tr = a.trace ? a.trace + 6 * (int64_t)w : nullptr;
+    if (tr && threadIdx.x == 0) {
+      tr[0] = global_ns();
+      tr[5] = (unsigned long long)blockIdx.x;
+    }
     if (w < a.nbt) {
       int I, J, K;
       unpack_bt(a.bt_list[w], I, J, K);
@@ -512,24 +740,29 @@ __global__ void __launch_bounds__(TileCfg<B>::NT) k_sweep_flow(TiledArgs<T> a, i
       const int64_t tIJ = tile_index(a.nb, I, J), tIK = tile_index(a.nb, I, K), tJK = tile_index(a.nb, J, K);
       const int64_t u1 = (K == J) ? -1 : tIK, u2 = (I == J) ? -1 : tJK;
       if (threadIdx.x == 0) sm.flag = wait_tiles(tile_cnt, tIJ, u1, u2, g, a.ctl, a.timeout_ns, g);
+      if (tr && threadIdx.x == 0) tr[1] = global_ns();
       __syncthreads();
       if (!sm.flag) return;
-      flow_block_triple<T, UNITW, B, false>(a, w, I, J, K, sm);
-      if (first && (int)blockIdx.x == a.skip_cta) return;   // fault injection: never release
-      if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(tile_cnt + tIJ, 1);
-        if (u1 >= 0) atomicAdd(tile_cnt + u1, 1);
-        if (u2 >= 0) atomicAdd(tile_cnt + u2, 1);
+      flow_block_triple<T, UNITW, B, NT>(a, w, I, J, K, sm);
+      if (tr && threadIdx.x == 0) {
+        tr[2] = global_ns();
+        tr[4] = (unsigned long long)sm.total;
       }
+      if (first && (int)blockIdx.x == a.skip_cta) return;   // fault injection: never release
+      if (threadIdx.x == 0) release_tiles(tile_cnt, tIJ, u1, u2);
+      if (tr && threadIdx.x == 0) tr[3] = global_ns();
     } else {
       const int tl = w - a.nbt;
       if (threadIdx.x == 0) sm.flag = wait_tiles(tile_cnt, tl, -1, -1, a.nb, a.ctl, a.timeout_ns, a.nb);
       __syncthreads();
       if (!sm.flag) return;
-      flow_pair_tile<T, B, false>(a, tl);
+      flow_pair_tile<T, B, NT>(a, tl);
     }
     first = false;
+    if (threadIdx.x == 0) sm.item = nxt;
+    __syncthreads();
+    w = sm.item;
+    __syncthreads();
   }
 }
 
@@ -560,21 +793,16 @@ __global__ void __launch_bounds__(256) k_sweep_warpflow(TiledArgs<T> a, int* flo
       if (lane == 0) ok = wait_tiles(tile_cnt, tIJ, u1, u2, g, a.ctl, a.timeout_ns, g);
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) return;
-      flow_block_triple<T, UNITW, B, true>(a, w, I, J, K, sm);
+      flow_block_triple<T, UNITW, B, 32>(a, w, I, J, K, sm);
       if (first && (int)blockIdx.x == a.skip_cta) return;   // fault injection: never release
-      if (lane == 0) {
-        __threadfence();
-        atomicAdd(tile_cnt + tIJ, 1);
-        if (u1 >= 0) atomicAdd(tile_cnt + u1, 1);
-        if (u2 >= 0) atomicAdd(tile_cnt + u2, 1);
-      }
+      if (lane == 0) release_tiles(tile_cnt, tIJ, u1, u2);
     } else {
       const int tl = w - a.nbt;
       int ok = 0;
       if (lane == 0) ok = wait_tiles(tile_cnt, tl, -1, -1, a.nb, a.ctl, a.timeout_ns, a.nb);
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) return;
-      flow_pair_tile<T, B, true>(a, tl);
+      flow_pair_tile<T, B, 32>(a, tl);
       __syncwarp();
     }
     first = false;
@@ -736,13 +964,49 @@ __device__ __forceinline__ void pair_unrank(int64_t n, int64_t p, int& i, int& j
   j = (int)(p - pair_index(n, i, i + 1)) + i + 1;
 }
 
+// Caller labels -> internal labels.  `lab` (n ints, or null for the
+// identity) is the relabeling of the tiled schedule; the pair comes back in
+// increasing internal order.
+__device__ __forceinline__ void map_pair(const int* lab, int& i, int& j) {
+  if (lab) {
+    const int a = lab[i], b = lab[j];
+    i = min(a, b);
+    j = max(a, b);
+  }
+}
+
+// Same for a triplet i<j<k; rowmap[r] is the internal row (0: hyp uv,
+// 1: hyp uw, 2: hyp vw of the sorted internal labels u<v<w) of the caller's
+// row r (0: hyp ij, 1: hyp ik, 2: hyp jk).  A row is named by its hypotenuse
+// pair, i.e. by the label it leaves out: leaving out the largest is row 0,
+// the middle one row 1, the smallest row 2.
+__device__ __forceinline__ void map_triplet(const int* lab, int& i, int& j, int& k, int* rowmap) {
+  if (!lab) {
+    rowmap[0] = 0;
+    rowmap[1] = 1;
+    rowmap[2] = 2;
+    return;
+  }
+  const int a = lab[i], b = lab[j], c = lab[k];
+  const int u = min(a, min(b, c)), w = max(a, max(b, c)), v = a + b + c - u - w;
+  auto out = [&](int third) { return third == w ? 0 : (third == v ? 1 : 2); };
+  rowmap[0] = out(c);   // hyp ij leaves out k
+  rowmap[1] = out(b);   // hyp ik leaves out j
+  rowmap[2] = out(a);   // hyp jk leaves out i
+  i = u;
+  j = v;
+  k = w;
+}
+
 // dir 0: tile-major (x, f) -> packed double buffers; dir 1: the reverse.
 template <typename T>
-__global__ void k_pairs_layout(T* x, T* f, int n, int nb, int B, double* px, double* pf, int dir) {
+__global__ void k_pairs_layout(T* x, T* f, int n, int nb, int B, double* px, double* pf, int dir,
+                               const int* lab) {
   const int64_t P = ch2(n);
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
     int i, j;
     pair_unrank(n, p, i, j);
+    map_pair(lab, i, j);
     const int64_t e = tiled_offset(nb, B, i, j);
     if (dir == 0) {
       if (px) px[p] = (double)x[e];
@@ -756,11 +1020,13 @@ __global__ void k_pairs_layout(T* x, T* f, int n, int nb, int B, double* px, dou
 
 // Packed d, w (device, double) -> tile-major d and W^{-1}.
 template <typename T>
-__global__ void k_load_problem(const double* pd, const double* pw, int n, int nb, int B, T* d, T* winv) {
+__global__ void k_load_problem(const double* pd, const double* pw, int n, int nb, int B, T* d, T* winv,
+                               const int* lab) {
   const int64_t P = ch2(n);
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
     int i, j;
     pair_unrank(n, p, i, j);
+    map_pair(lab, i, j);
     const int64_t e = tiled_offset(nb, B, i, j);
     d[e] = (T)pd[p];
     winv[e] = (T)(1.0 / pw[p]);
@@ -792,11 +1058,12 @@ __global__ void k_fill(T* p, int64_t count, T v) {
 // dir 0: buf[3q + r] = scale * z;  dir 1: z = buf[3q + r] / scale.
 template <typename T, int B>
 __global__ void k_tri_duals_tiled(T* zt, const int* bt_rank, int n, int nb, int64_t first, int64_t count,
-                                  double* buf, double scale, int dir) {
+                                  double* buf, double scale, int dir, const int* lab) {
   constexpr int BB = B * B;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += (int64_t)gridDim.x * blockDim.x) {
-    int i, j, k;
+    int i, j, k, rm[3];
     tri_unrank(n, first + q, i, j, k);
+    map_triplet(lab, i, j, k, rm);
     const int I = i / B, J = j / B, K = k / B;
     const int la = i % B, lb = j % B, lc = k % B;
     const int t = (la + lb + lc) % B;
@@ -804,20 +1071,22 @@ __global__ void k_tri_duals_tiled(T* zt, const int* bt_rank, int n, int nb, int6
     const int64_t base = w * (3 * B * BB) + (int64_t)t * (3 * BB) + la * B + lb;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      if (dir == 0) buf[3 * q + r] = scale * (double)zt[base + r * BB];
-      else zt[base + r * BB] = (T)(buf[3 * q + r] / scale);
+      if (dir == 0) buf[3 * q + r] = scale * (double)zt[base + rm[r] * BB];
+      else zt[base + rm[r] * BB] = (T)(buf[3 * q + r] / scale);
     }
   }
 }
 
 // Pair duals between the tiled store and packed order (2 per pair).
 template <typename T>
-__global__ void k_pair_duals_tiled(T* zp, int n, int nb, int B, double* buf, double scale, int dir) {
+__global__ void k_pair_duals_tiled(T* zp, int n, int nb, int B, double* buf, double scale, int dir,
+                                   const int* lab) {
   const int64_t P = ch2(n);
   const int BB = B * B;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
     int i, j;
     pair_unrank(n, p, i, j);
+    map_pair(lab, i, j);
     const int64_t tl = tile_index(nb, i / B, j / B);
     const int64_t e = tl * (2 * BB) + (i % B) * B + (j % B);
     if (dir == 0) {

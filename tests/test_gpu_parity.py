@@ -19,7 +19,10 @@ TOL_SWEEP = 1e-12
 
 
 def _solver(n, d, w, **kw):
+    """Tiled schedule on consecutive blocks (no relabeling), the order the
+    oracle's schedule 2 walks; the relabeled order is tested separately."""
     import paper_1901_10084_gb300 as cc
+    kw.setdefault("interleave", False)
     return cc.Solver(n, d, w, **kw)
 
 
@@ -117,12 +120,12 @@ def test_paper_schedules_converge_planted60(schedule):
 
 # ---------------------------------------------------------------- fused form
 
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("n,tile,weighted,pre", [(60, 16, False, 3), (61, 16, True, 5),
                                                  (200, 16, False, 2), (150, 8, True, 2),
                                                  (90, 8, True, 4), (203, 8, False, 6)])
 def test_fused_one_sweep_from_identical_state(n, tile, weighted, pre, variant):
-    """variant 1: one CTA per block triple; 2: one warp per block triple."""
+    """variant 1: one CTA per block triple; 2: one warp; 3: a half-size CTA."""
     d, w, _ = chung_lu(n, 2.5, 8.0, seed=n, weights=(0.5, 2.0) if weighted else None)
     o = oracle.State(n, d, w, 0.2)
     for _ in range(pre):

@@ -10,7 +10,10 @@ pytestmark = pytest.mark.gpu
 
 
 def _solver(n, d, w, **kw):
+    """Tiled schedule on consecutive blocks (no relabeling), the order the
+    oracle's schedule 2 walks; the relabeled order is tested separately."""
     import paper_1901_10084_gb300 as cc
+    kw.setdefault("interleave", False)
     return cc.Solver(n, d, w, **kw)
 
 
