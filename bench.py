@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-precision-form", action="store_true",
                    help="skip the FP32 bulk + FP64 refinement time-to-tolerance solve")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
+    p.add_argument("--batch-count", type=int, default=256)
     return p.parse_args()
 
 
@@ -231,11 +233,72 @@ def run_ours(args, rank, world, local_rank):
                 "max_violation": pf["max_violation"],
                 "reference": "the plain FP64 GPU solve above (itself pinned to the oracle sweep by sweep)"}
             pf["speedup_vs_fp64"] = ref["seconds"] / pf["seconds"]
+            # both forms to a tighter tolerance: the LP objectives then agree to 1e-6
+            tight = argparse.Namespace(**vars(args))
+            tight.tol = 1e-7
+            r64, _ = _time_to_tol(tight, n, d, w, stream, "fp64")
+            r32, _ = _time_to_tol(tight, n, d, w, stream, "fp32_refine")
+            pf["tol_1e-7"] = {"fp64_seconds": r64["seconds"], "fp32_refine_seconds": r32["seconds"],
+                              "fp64_sweeps": r64["sweeps"], "fp32_refine_sweeps": r32["sweeps"],
+                              "lp_objective_rel": abs(r32["lp_objective"] - r64["lp_objective"])
+                              / abs(r64["lp_objective"])}
             out["precision_form"] = pf
+    if rank == 0 and not args.no_batch and args.schedule == "tiled":
+        out["batched_form"] = _batched(args, stream)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
     return out
+
+
+def _batched(args, stream):
+    """The batched form: `batch_count` planted-partition instances with
+    n ~ U[50, 400], k ~ U[2, 8] clusters, p_in 0.7, p_out 0.05 (seed 3), in one
+    launch per sweep; tile and work-list order from the autotuner."""
+    import numpy as np
+    import torch
+
+    import paper_1901_10084_gb300 as cc
+    from instances import batch_planted
+    inst = batch_planted(args.batch_count, 50, 400, 2, 8, 0.7, 0.05, seed=3)
+    T = sum(n * (n - 1) * (n - 2) // 6 for n, _, _ in inst)
+    t = time.perf_counter()
+    opts, tune_ms = cc.autotune_batch(inst, trial_sweeps=3)
+    tune_s = time.perf_counter() - t
+    rec = {"instances": len(inst), "triplets_per_sweep": T, "autotuned": opts,
+           "autotune_ms_per_sweep": tune_ms, "autotune_seconds": tune_s,
+           "desc": "planted partition, n~U[50,400], k~U[2,8], p 0.7/0.05, seed 3, unit weights"}
+    with cc.Batch(inst, stream=stream, check_every=args.check_every, **opts) as b:
+        b.sweep(3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.sweep(20)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+    rec["sweep_ms"] = ms
+    rec["value"] = T / (ms * 1e-3)
+    rec["unit"] = UNIT
+    for prec in ("fp64", "fp32_refine"):
+        with cc.Batch(inst, stream=stream, check_every=args.check_every, precision=prec, **opts) as b:
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            conv, done, per = b.solve(args.tol, 20000)
+            torch.cuda.synchronize()
+            rec[f"time_to_tol_{prec}"] = {"seconds": time.perf_counter() - t, "batch_sweeps": done,
+                                          "converged": conv, "max_instance_sweeps": max(per),
+                                          "median_instance_sweeps": float(np.median(per))}
+    # the same instances one by one (a sample), to show what batching buys
+    sample = inst[:: max(1, len(inst) // 16)]
+    t = time.perf_counter()
+    for n, d, w in sample:
+        with cc.Solver(n, d, w, stream=stream, check_every=args.check_every, tile=opts["tile"]) as s1:
+            s1.solve(args.tol, 20000)
+    torch.cuda.synchronize()
+    one = (time.perf_counter() - t) / len(sample)
+    rec["sequential_estimate"] = {"seconds": one * len(inst), "sample": len(sample),
+                                  "note": "mean single-instance FP64 solve time of the sample x instances"}
+    return rec
 
 
 def _profiled_traffic(args):

@@ -106,6 +106,9 @@ typedef struct cc_opts {
                                tiled order on the internal labels.  0 = blocks
                                of consecutive objects.  Default 1.  Results
                                are always exchanged in caller labels. */
+  int32_t batch_order;      /* batches: order of the shared work list.  0 =
+                               phase-major (phase g of every instance, then
+                               the next phase), 1 = instance-major.  Default 0. */
 } cc_opts;
 
 typedef struct cc_stats {
@@ -225,6 +228,55 @@ int64_t cc_device_bytes(const cc_handle* h);
  * in cc_last_error(NULL). */
 int cc_check_noalloc(int64_t n, double eps, const double* x, const double* f, const double* d,
                      const double* w, const double* y_pair, double* out, void* stream);
+
+/* ---- batches: many instances of uneven size, one launch per sweep -------
+ * Survey row "batched form"; the paper has one instance per run.  A batch
+ * owns one handle per instance (all with the same options: tiled schedule,
+ * fused form, same tile and precision); every sweep of the batch is one
+ * cooperative launch that drains a single work list holding the block
+ * triples and pair tiles of all active instances (two launches while some
+ * instances are in FP32 state and others in FP64).  Each instance keeps its
+ * own dataflow counters, so its result is the same as a sweep of the handle
+ * on its own. */
+typedef struct cc_batch cc_batch;
+
+/* Create count instances: ns[i] objects, ds[i] / ws[i] host arrays of
+ * ns[i](ns[i]-1)/2 doubles (packed order, copied).  opts as for cc_create
+ * (NULL = defaults). */
+int cc_batch_create(cc_batch** out, int32_t count, const int64_t* ns, const double* const* ds,
+                    const double* const* ws, const cc_opts* opts);
+
+/* Number of instances. */
+int32_t cc_batch_size(const cc_batch* b);
+
+/* Borrowed handle of instance i (for cc_get_x, cc_get_duals, cc_check,
+ * cc_set_state, ...; not for cc_destroy).  NULL when i is out of range. */
+cc_handle* cc_batch_handle(cc_batch* b, int32_t i);
+
+/* k sweeps of every instance (asynchronous, like cc_sweep). */
+int cc_batch_sweep(cc_batch* b, int64_t k);
+
+/* Sweep all instances, checking each every check_every sweeps; an instance
+ * leaves the work list once its violation is <= tol (after its FP64
+ * refinement in CC_PREC_FP32_REFINE).  *sweeps_done (nullable): batch sweeps
+ * run; per_instance (nullable, count entries): sweeps each instance needed,
+ * -1 if it did not converge.  CC_ERR_NOT_CONVERGED if any did not. */
+int cc_batch_solve(cc_batch* b, double tol, int64_t max_sweeps, int64_t* sweeps_done, int64_t* per_instance);
+
+/* Autotuner: times trial_sweeps batch sweeps (after as many warm-up sweeps)
+ * for every tile in {8, 16, 32} and work-list order in {0, 1} on the given
+ * instances and writes the fastest options (base with tile and batch_order
+ * replaced) to *best, its time per sweep in ms to *best_ms (nullable).  The
+ * tile changes the visiting order, hence the iterates; only sweep time is
+ * compared. */
+int cc_batch_autotune(int32_t count, const int64_t* ns, const double* const* ds, const double* const* ws,
+                      const cc_opts* base, int32_t trial_sweeps, cc_opts* best, double* best_ms);
+
+/* Destroy the batch and its handles.  NULL is a no-op. */
+void cc_batch_destroy(cc_batch* b);
+
+/* Message of the last failed call on b (NULL: of the last failed create). */
+const char* cc_batch_last_error(const cc_batch* b);
 
 /* Release everything the handle owns.  NULL is a no-op. */
 void cc_destroy(cc_handle* h);

@@ -21,7 +21,7 @@ from ._native import (CCError, CC_OK, CC_ERR_ARG, CC_ERR_OOM, CC_ERR_CUDA, CC_ER
 from .buildlib import build
 
 __all__ = [
-    "Solver", "CCError", "build", "num_pairs", "num_triplets",
+    "Solver", "Batch", "autotune_batch", "CCError", "build", "num_pairs", "num_triplets",
     "cc_opts_default", "cc_create", "cc_create_device", "cc_sweep", "cc_check", "cc_solve",
     "cc_get_x", "cc_get_duals", "cc_set_state", "cc_get_stats", "cc_device_bytes",
     "cc_destroy", "cc_last_error", "cc_refine_fp64", "cc_set_duals", "cc_check_noalloc",
@@ -160,7 +160,17 @@ class Solver:
     def device_bytes(self) -> int:
         return cc_device_bytes(self.h)
 
+    @classmethod
+    def _borrow(cls, h, n, eps):
+        """A view of a handle owned elsewhere (an instance of a Batch)."""
+        s = cls.__new__(cls)
+        s.h, s.n, s.eps, s._borrowed, s._alloc = h, int(n), float(eps), True, None
+        return s
+
     def close(self) -> None:
+        if getattr(self, "_borrowed", False):
+            self.h = None
+            return
         if getattr(self, "h", None) is not None:
             cc_destroy(self.h)
             self.h = None
@@ -176,3 +186,84 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Batch:
+    """Many correlation-clustering instances of uneven size swept together:
+    one launch per sweep drains the work of every active instance.
+
+    ``instances`` is a list of (n, d, w); keyword options as for Solver (the
+    tiled schedule and the fused form are required).  ``instance(i)`` gives
+    a Solver view of instance i (get_x, get_duals, check, set_state ...)."""
+
+    def __init__(self, instances, eps=0.2, tile=16, precision="fp64", check_every=10, device=0,
+                 stream=None, torch_alloc=True, interleave=True, batch_order=0, grid=0):
+        import torch
+        o = cc_opts_default()
+        o.eps = float(eps)
+        o.tile = int(tile)
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.check_every = int(check_every)
+        o.device = int(device)
+        o.interleave = 1 if interleave else 0
+        o.batch_order = int(batch_order)
+        o.grid = int(grid)
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        o.stream = ctypes.c_void_p(int(stream.cuda_stream))
+        self.stream = stream
+        self._alloc = None
+        if torch_alloc:
+            self._alloc = _TorchAllocator(device)
+            o.alloc = self._alloc.alloc
+            o.free = self._alloc.free
+        self.opts = o
+        self.ns = [int(n) for n, _, _ in instances]
+        self.eps = float(eps)
+        self.b = _native.cc_batch_create(self.ns, [d for _, d, _ in instances], [w for _, _, w in instances], o)
+
+    def __len__(self):
+        return len(self.ns)
+
+    def instance(self, i: int) -> Solver:
+        return Solver._borrow(_native.cc_batch_handle(self.b, i), self.ns[i], self.eps)
+
+    def sweep(self, k: int = 1) -> None:
+        _native.cc_batch_sweep(self.b, k)
+
+    def solve(self, tol: float, max_sweeps: int):
+        """Returns (all converged, batch sweeps, sweeps per instance)."""
+        rc, done, per = _native.cc_batch_solve(self.b, tol, max_sweeps)
+        return rc == CC_OK, done, per
+
+    def close(self) -> None:
+        if getattr(self, "b", None) is not None:
+            _native.cc_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def autotune_batch(instances, trial_sweeps=5, **kw):
+    """Pick tile and work-list order for a batch by timing trial sweeps;
+    returns (options dict for Batch, ms per sweep)."""
+    import torch
+    o = cc_opts_default()
+    o.eps = float(kw.get("eps", 0.2))
+    o.precision = PRECISIONS[kw.get("precision", "fp64")]
+    o.interleave = 1 if kw.get("interleave", True) else 0
+    stream = torch.cuda.current_stream()
+    o.stream = ctypes.c_void_p(int(stream.cuda_stream))
+    best, ms = _native.cc_batch_autotune([n for n, _, _ in instances], [d for _, d, _ in instances],
+                                         [w for _, _, w in instances], o, trial_sweeps)
+    return {"tile": best.tile, "batch_order": best.batch_order}, ms

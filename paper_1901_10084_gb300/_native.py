@@ -51,6 +51,7 @@ class cc_opts(ctypes.Structure):
         ("refine_at", ctypes.c_double),
         ("trace", ctypes.c_int32),
         ("interleave", ctypes.c_int32),
+        ("batch_order", ctypes.c_int32),
     ]
 
 
@@ -76,7 +77,9 @@ class cc_stats(ctypes.Structure):
 EXPORTS = ("cc_opts_default", "cc_create", "cc_create_device", "cc_sweep", "cc_check",
            "cc_solve", "cc_get_x", "cc_get_duals", "cc_set_state", "cc_get_stats",
            "cc_device_bytes", "cc_destroy", "cc_last_error", "cc_check_noalloc",
-           "cc_refine_fp64", "cc_set_duals", "cc_get_trace")
+           "cc_refine_fp64", "cc_set_duals", "cc_get_trace", "cc_batch_create", "cc_batch_size",
+           "cc_batch_handle", "cc_batch_sweep", "cc_batch_solve", "cc_batch_autotune", "cc_batch_destroy",
+           "cc_batch_last_error")
 
 _lib = None
 _lock = threading.Lock()
@@ -128,6 +131,25 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         lib.cc_destroy.restype = None
         lib.cc_last_error.argtypes = [H]
         lib.cc_last_error.restype = ctypes.c_char_p
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        I64P = ctypes.POINTER(ctypes.c_int64)
+        lib.cc_batch_create.argtypes = [HP, ctypes.c_int32, I64P, PP, PP, ctypes.POINTER(cc_opts)]
+        lib.cc_batch_create.restype = ctypes.c_int
+        lib.cc_batch_size.argtypes = [H]
+        lib.cc_batch_size.restype = ctypes.c_int32
+        lib.cc_batch_handle.argtypes = [H, ctypes.c_int32]
+        lib.cc_batch_handle.restype = ctypes.c_void_p
+        lib.cc_batch_sweep.argtypes = [H, i64]
+        lib.cc_batch_sweep.restype = ctypes.c_int
+        lib.cc_batch_solve.argtypes = [H, ctypes.c_double, i64, I64P, I64P]
+        lib.cc_batch_solve.restype = ctypes.c_int
+        lib.cc_batch_autotune.argtypes = [ctypes.c_int32, I64P, PP, PP, ctypes.POINTER(cc_opts), ctypes.c_int32,
+                                          ctypes.POINTER(cc_opts), ctypes.POINTER(ctypes.c_double)]
+        lib.cc_batch_autotune.restype = ctypes.c_int
+        lib.cc_batch_destroy.argtypes = [H]
+        lib.cc_batch_destroy.restype = None
+        lib.cc_batch_last_error.argtypes = [H]
+        lib.cc_batch_last_error.restype = ctypes.c_char_p
         lib.cc_get_trace.argtypes = [H, ctypes.POINTER(ctypes.c_uint64), i64]
         lib.cc_get_trace.restype = i64
         lib.cc_refine_fp64.argtypes = [H]
@@ -261,3 +283,72 @@ def cc_check_noalloc(n: int, eps: float, x_ptr: int, f_ptr: int, d_ptr: int, w_p
     v = ctypes.c_void_p
     return int(load().cc_check_noalloc(n, eps, v(x_ptr), v(f_ptr), v(d_ptr), v(w_ptr),
                                        v(y_pair_ptr), v(out_ptr), v(stream)))
+
+
+# ---- batches ---------------------------------------------------------------
+
+def _batch_arrays(ns, ds, ws):
+    import numpy as np
+    count = len(ns)
+    keep = [np.ascontiguousarray(a, dtype=np.float64) for a in list(ds) + list(ws)]
+    n_arr = (ctypes.c_int64 * count)(*[int(v) for v in ns])
+    d_arr = (ctypes.c_void_p * count)(*[a.ctypes.data for a in keep[:count]])
+    w_arr = (ctypes.c_void_p * count)(*[a.ctypes.data for a in keep[count:]])
+    return count, n_arr, d_arr, w_arr, keep
+
+
+def _bcheck(rc: int, b) -> None:
+    if rc != CC_OK:
+        msg = load().cc_batch_last_error(b)
+        raise CCError(rc, msg.decode() if msg else "")
+
+
+def cc_batch_create(ns, ds, ws, opts: cc_opts | None = None):
+    count, n_arr, d_arr, w_arr, keep = _batch_arrays(ns, ds, ws)
+    b = ctypes.c_void_p()
+    rc = load().cc_batch_create(ctypes.byref(b), count, n_arr, d_arr, w_arr,
+                                ctypes.byref(opts) if opts else None)
+    _bcheck(rc, None)
+    return b
+
+
+def cc_batch_size(b) -> int:
+    return int(load().cc_batch_size(b))
+
+
+def cc_batch_handle(b, i: int):
+    return ctypes.c_void_p(load().cc_batch_handle(b, i))
+
+
+def cc_batch_sweep(b, k: int) -> None:
+    _bcheck(load().cc_batch_sweep(b, k), b)
+
+
+def cc_batch_solve(b, tol: float, max_sweeps: int):
+    """Returns (status, batch sweeps, sweeps per instance)."""
+    count = cc_batch_size(b)
+    per = (ctypes.c_int64 * count)()
+    done = ctypes.c_int64(0)
+    rc = load().cc_batch_solve(b, tol, max_sweeps, ctypes.byref(done), per)
+    if rc not in (CC_OK, CC_ERR_NOT_CONVERGED):
+        _bcheck(rc, b)
+    return rc, done.value, list(per)
+
+
+def cc_batch_autotune(ns, ds, ws, base: cc_opts | None, trial_sweeps: int):
+    count, n_arr, d_arr, w_arr, keep = _batch_arrays(ns, ds, ws)
+    best = cc_opts()
+    ms = ctypes.c_double(0.0)
+    rc = load().cc_batch_autotune(count, n_arr, d_arr, w_arr, ctypes.byref(base) if base else None,
+                                  trial_sweeps, ctypes.byref(best), ctypes.byref(ms))
+    _bcheck(rc, None)
+    return best, ms.value
+
+
+def cc_batch_destroy(b) -> None:
+    load().cc_batch_destroy(b)
+
+
+def cc_batch_last_error(b=None) -> str:
+    m = load().cc_batch_last_error(b)
+    return m.decode() if m else ""

@@ -58,6 +58,7 @@ struct cc_handle {
   int* flow = nullptr;       // dataflow sweep: item counter + visits per tile
   unsigned long long* trace = nullptr;   // per-item timestamps of the last sweep (opts.trace)
   int* lab = nullptr;        // caller label -> internal label (tiled schedule, opts.interleave)
+  std::vector<int> h_bt_off; // host copy of the phase offsets of the block triples
   // schedules 0 and 1 (device tables)
   ListArgs la{};
   int* l_pre1 = nullptr;
@@ -73,7 +74,8 @@ struct cc_handle {
   int part_cap = 0;
   double* stage = nullptr;   // layout staging
   int64_t stage_elems = 0;
-  double* h_pin = nullptr;   // pinned host mirror of small results
+  double* h_pin = nullptr;   // pinned host mirror of the check partials (part_cap * 6)
+  int chk_gtri = 0, chk_gpair = 0;
   // launch config
   int sweep_grid = 0, sweep_threads = 0;
   // bookkeeping
@@ -338,6 +340,7 @@ int build_tables(cc_handle* h) {
     h->max_bt_phase = std::max(h->max_bt_phase, (int)list.size() - off[g]);
   }
   off[nb] = (int)list.size();
+  h->h_bt_off = off;
   for (int I = 0; I < nb; ++I)
     for (int J = I; J < nb; ++J) tiles.push_back(I | (J << 16));
   h->nbt = (int)list.size();
@@ -548,7 +551,7 @@ int create_common(cc_handle** out, int64_t n, const double* d_dev, const double*
   h->part = (double*)dalloc(h, (size_t)h->part_cap * 6 * sizeof(double));  // maxima, then 5 sums each
   if (!h->x || !h->f || !h->d64 || !h->winv64 || !h->d || !h->winv || !h->zp || !h->zt || !h->ctl || !h->part)
     return fail(h, CC_ERR_OOM, "device state");
-  CK(h, cudaMallocHost((void**)&h->h_pin, 64 * sizeof(double)));
+  CK(h, cudaMallocHost((void**)&h->h_pin, (size_t)h->part_cap * 6 * sizeof(double)));
   CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->st));
   CK(h, cudaMemsetAsync(h->d64, 0, te * sizeof(double), h->st));
   k_fill<double><<<grid_for(h, te, 256), 256, 0, h->st>>>(h->winv64, te, 1.0);
@@ -697,6 +700,7 @@ void cc_opts_default(cc_opts* o) {
   o->refine_at = 1e-5;
   o->trace = 0;
   o->interleave = 1;
+  o->batch_order = 0;
 }
 
 int cc_create_device(cc_handle** out, int64_t n, const double* d_dev, const double* w_dev, const cc_opts* opts) {
@@ -766,14 +770,19 @@ int cc_sweep(cc_handle* h, int64_t k) {
   return CC_OK;
 }
 
-int cc_check(cc_handle* h, cc_stats* st) {
-  if (!h) return fail(nullptr, CC_ERR_ARG, "handle is NULL");
-  CK(h, cudaSetDevice(h->dev));
-  int rc = read_ctl_error(h);
-  if (rc) return rc;
+}  // extern "C"
+
+namespace {
+
+// Convergence check in two halves: the launch queues the reduction kernels and
+// the copy of their partials into pinned host memory on the handle's stream;
+// the finish (after the stream is synchronized) folds the partials.
+int check_launch(cc_handle* h) {
   const int B = h->B;
   const int gtri = std::min(h->part_cap, h->sms * 4);
   const int gpair = std::min(h->part_cap, grid_for(h, h->tile_elems, 256));
+  h->chk_gtri = gtri;
+  h->chk_gpair = gpair;
   double* pm = h->part;                        // gtri maxima
   double* ps = h->part + h->part_cap;          // gpair x 5 sums
   const double yscale = h->o.exact ? 1.0 : h->o.eps;
@@ -790,13 +799,18 @@ int cc_check(cc_handle* h, cc_stats* st) {
   }
 #undef LAUNCH_CHECK
   CK(h, cudaGetLastError());
-  std::vector<double> hm(gtri), hs((size_t)gpair * 5);
-  CK(h, cudaMemcpyAsync(hm.data(), pm, gtri * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-  CK(h, cudaMemcpyAsync(hs.data(), ps, (size_t)gpair * 5 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-  CK(h, cudaStreamSynchronize(h->st));
+  CK(h, cudaMemcpyAsync(h->h_pin, pm, gtri * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaMemcpyAsync(h->h_pin + h->part_cap, ps, (size_t)gpair * 5 * sizeof(double), cudaMemcpyDeviceToHost,
+                        h->st));
+  return CC_OK;
+}
+
+void check_finish(cc_handle* h, cc_stats* st) {
+  const double* hm = h->h_pin;
+  const double* hs = h->h_pin + h->part_cap;
   double mv = 0, lp = 0, wf = 0, quad = 0, by = 0, pv = 0;
-  for (int i = 0; i < gtri; ++i) mv = std::max(mv, hm[i]);
-  for (int i = 0; i < gpair; ++i) {
+  for (int i = 0; i < h->chk_gtri; ++i) mv = std::max(mv, hm[i]);
+  for (int i = 0; i < h->chk_gpair; ++i) {
     lp += hs[5 * i];
     wf += hs[5 * i + 1];
     quad += hs[5 * i + 2];
@@ -819,6 +833,21 @@ int cc_check(cc_handle* h, cc_stats* st) {
     if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) s.last_sweep_ms = ms;
   }
   if (st) *st = s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cc_check(cc_handle* h, cc_stats* st) {
+  if (!h) return fail(nullptr, CC_ERR_ARG, "handle is NULL");
+  CK(h, cudaSetDevice(h->dev));
+  int rc = read_ctl_error(h);
+  if (rc) return rc;
+  rc = check_launch(h);
+  if (rc) return rc;
+  CK(h, cudaStreamSynchronize(h->st));
+  check_finish(h, st);
   return CC_OK;
 }
 
@@ -1043,6 +1072,359 @@ void cc_destroy(cc_handle* h) {
 const char* cc_last_error(const cc_handle* h) {
   if (!h) return g_create_error.c_str();
   return h->err.c_str();
+}
+
+}  // extern "C"
+
+// ====================================================================== batch
+//
+// Many instances of uneven size in one launch per sweep (k_sweep_batch): a
+// batch owns ordinary handles (same options: tiled schedule, fused form,
+// same tile) and drains one queue of work items from all instances that are
+// still active.  Instances in FP32 state and in FP64 state run in separate
+// launches of the same sweep.
+
+struct cc_batch {
+  std::vector<cc_handle*> hs;
+  std::vector<char> active;
+  std::vector<double> prev_fp32;       // last FP32 violation per instance (stall test)
+  cc_opts o{};
+  cudaStream_t st = nullptr;
+  int dev = 0, sms = 0;
+  bool unitw = true;
+  // device buffers, allocated through hs[0]'s allocator
+  void* args[2] = {nullptr, nullptr};  // TiledArgs<double>, TiledArgs<float> per instance
+  int2* items[2] = {nullptr, nullptr};
+  int nitems[2] = {0, 0};
+  bool stale[2] = {true, true};
+  int* cnt = nullptr;                  // [0]: item counter; then every instance's tile counters
+  std::vector<int64_t> cnt_off;
+  int64_t cnt_total = 0;
+  int64_t sweeps = 0;
+  std::string err;
+};
+
+namespace {
+
+int bfail(cc_batch* b, int code, const std::string& msg) {
+  if (b) b->err = msg; else g_create_error = msg;
+  return code;
+}
+
+#define BCK(b, call)                                                                  \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) return bfail(b, CC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Work-item list of one precision group: (instance, local item).  Order 0
+// ("phase-major"): phase g of every instance, g = 0, 1, ..., then all pair
+// tiles; order 1 ("instance-major"): every instance's items in turn.  Both
+// keep each instance's items in its own order.
+void build_items(cc_batch* b, bool fp32, std::vector<int2>& out) {
+  out.clear();
+  std::vector<int> ids;
+  int maxnb = 0;
+  for (size_t i = 0; i < b->hs.size(); ++i)
+    if (b->active[i] && b->hs[i]->fp32 == fp32) {
+      ids.push_back((int)i);
+      maxnb = std::max(maxnb, b->hs[i]->nb);
+    }
+  if (b->o.batch_order == 1) {
+    for (int i : ids) {
+      const cc_handle* h = b->hs[i];
+      for (int w = 0; w < h->nbt + h->ntiles; ++w) out.push_back(make_int2(i, w));
+    }
+    return;
+  }
+  for (int g = 0; g < maxnb; ++g)
+    for (int i : ids) {
+      const cc_handle* h = b->hs[i];
+      if (g >= h->nb) continue;
+      for (int w = h->h_bt_off[g]; w < h->h_bt_off[g + 1]; ++w) out.push_back(make_int2(i, w));
+    }
+  for (int i : ids) {
+    const cc_handle* h = b->hs[i];
+    for (int tl = 0; tl < h->ntiles; ++tl) out.push_back(make_int2(i, h->nbt + tl));
+  }
+}
+
+template <typename T>
+int upload_group(cc_batch* b, int gi) {
+  const bool fp32 = gi == 1;
+  std::vector<TiledArgs<T>> args(b->hs.size());
+  for (size_t i = 0; i < b->hs.size(); ++i) {
+    cc_handle* h = b->hs[i];
+    if (h->fp32 != fp32) continue;
+    args[i] = tiled_args<T>(h);
+    args[i].cnt = b->cnt + b->cnt_off[i];
+    args[i].trace = nullptr;
+    args[i].skip_cta = -1;
+  }
+  std::vector<int2> items;
+  build_items(b, fp32, items);
+  cc_handle* h0 = b->hs[0];
+  if (!b->args[gi]) {
+    b->args[gi] = dalloc(h0, args.size() * sizeof(TiledArgs<T>));
+    if (!b->args[gi]) return bfail(b, CC_ERR_OOM, "batch arguments");
+  }
+  if (b->items[gi]) dfree(h0, b->items[gi]);
+  b->items[gi] = (int2*)dalloc(h0, std::max<size_t>(1, items.size()) * sizeof(int2));
+  if (!b->items[gi]) return bfail(b, CC_ERR_OOM, "batch work list");
+  BCK(b, cudaMemcpyAsync(b->args[gi], args.data(), args.size() * sizeof(TiledArgs<T>), cudaMemcpyHostToDevice, b->st));
+  if (!items.empty())
+    BCK(b, cudaMemcpyAsync(b->items[gi], items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, b->st));
+  BCK(b, cudaStreamSynchronize(b->st));
+  b->nitems[gi] = (int)items.size();
+  b->stale[gi] = false;
+  return CC_OK;
+}
+
+template <typename T, bool UNITW, int B>
+void* batch_kernel() {
+  return (void*)k_sweep_batch<T, UNITW, B, TileCfg<B>::NT>;
+}
+
+template <typename T>
+void* batch_kernel_b(bool unitw, int B) {
+  if (unitw) return B == 8 ? batch_kernel<T, true, 8>() : B == 16 ? batch_kernel<T, true, 16>() : batch_kernel<T, true, 32>();
+  return B == 8 ? batch_kernel<T, false, 8>() : B == 16 ? batch_kernel<T, false, 16>() : batch_kernel<T, false, 32>();
+}
+
+// One sweep of every active instance of one precision group.
+int batch_launch(cc_batch* b, int gi) {
+  int rc = CC_OK;
+  if (b->stale[gi]) rc = gi ? upload_group<float>(b, gi) : upload_group<double>(b, gi);
+  if (rc) return rc;
+  if (b->nitems[gi] == 0) return CC_OK;
+  const int B = b->o.tile;
+  void* k = gi ? batch_kernel_b<float>(b->unitw, B) : batch_kernel_b<double>(b->unitw, B);
+  const size_t smem = flow_smem(gi == 1, B);
+  const int threads = threads_for_tile(B);
+  BCK(b, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem));
+  if (per_sm < 1) return bfail(b, CC_ERR_CUDA, "batch kernel does not fit on an SM");
+  int grid = std::min(per_sm, 8) * b->sms;
+  if (b->o.grid > 0) grid = std::min(b->o.grid, per_sm * b->sms);
+  grid = std::min(grid, std::max(1, b->nitems[gi]));   // the tail of a solve has few items left
+  BCK(b, cudaMemsetAsync(b->cnt, 0, (size_t)b->cnt_total * sizeof(int), b->st));
+  void* a = b->args[gi];
+  int2* items = b->items[gi];
+  int total = b->nitems[gi];
+  int* next = b->cnt;
+  void* kargs[] = {&a, &items, &total, &next};
+  BCK(b, cudaLaunchCooperativeKernel(k, grid, threads, kargs, smem, b->st));
+  for (size_t i = 0; i < b->hs.size(); ++i) {
+    cc_handle* h = b->hs[i];
+    if (!b->active[i] || h->fp32 != (gi == 1)) continue;
+    h->sweeps++;
+    if (h->fp32) h->fp32_sweeps++;
+  }
+  return CC_OK;
+}
+
+int batch_sweep(cc_batch* b, int64_t k) {
+  BCK(b, cudaSetDevice(b->dev));
+  for (int64_t s = 0; s < k; ++s) {
+    int rc = batch_launch(b, 0);
+    if (rc) return rc;
+    rc = batch_launch(b, 1);
+    if (rc) return rc;
+    b->sweeps++;
+  }
+  return CC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cc_batch_destroy(cc_batch* b) {
+  if (!b) return;
+  if (!b->hs.empty()) {
+    cc_handle* h0 = b->hs[0];
+    cudaSetDevice(h0->dev);
+    cudaStreamSynchronize(b->st);
+    for (int g = 0; g < 2; ++g) {
+      dfree(h0, b->args[g]);
+      dfree(h0, b->items[g]);
+    }
+    dfree(h0, b->cnt);
+  }
+  for (cc_handle* h : b->hs) cc_destroy(h);
+  delete b;
+}
+
+int cc_batch_create(cc_batch** out, int32_t count, const int64_t* ns, const double* const* ds,
+                    const double* const* ws, const cc_opts* opts) {
+  if (!out) return bfail(nullptr, CC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !ns || !ds || !ws) return bfail(nullptr, CC_ERR_ARG, "count >= 1 and ns, ds, ws required");
+  cc_opts o;
+  cc_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.schedule != CC_SCHED_TILED || o.exact)
+    return bfail(nullptr, CC_ERR_ARG, "a batch runs the tiled schedule in the fused form");
+  cc_batch* b = new (std::nothrow) cc_batch();
+  if (!b) return bfail(nullptr, CC_ERR_OOM, "batch");
+  b->o = o;
+  b->st = (cudaStream_t)o.stream;
+  b->dev = o.device;
+  for (int32_t i = 0; i < count; ++i) {
+    cc_handle* h = nullptr;
+    int rc = cc_create(&h, ns[i], ds[i], ws[i], &o);
+    if (rc) {
+      std::string msg = "instance " + std::to_string(i) + ": " + g_create_error;
+      cc_batch_destroy(b);
+      return bfail(nullptr, rc, msg);
+    }
+    b->hs.push_back(h);
+    b->unitw = b->unitw && h->unitw;
+  }
+  b->sms = b->hs[0]->sms;
+  b->active.assign(count, 1);
+  b->prev_fp32.assign(count, INFINITY);
+  b->cnt_off.resize(count);
+  int64_t off = 1;
+  for (int32_t i = 0; i < count; ++i) {
+    b->cnt_off[i] = off;
+    off += b->hs[i]->ntiles;
+  }
+  b->cnt_total = off;
+  b->cnt = (int*)dalloc(b->hs[0], (size_t)off * sizeof(int));
+  if (!b->cnt) {
+    cc_batch_destroy(b);
+    return bfail(nullptr, CC_ERR_OOM, "batch counters");
+  }
+  *out = b;
+  return CC_OK;
+}
+
+int32_t cc_batch_size(const cc_batch* b) { return b ? (int32_t)b->hs.size() : 0; }
+
+cc_handle* cc_batch_handle(cc_batch* b, int32_t i) {
+  if (!b || i < 0 || i >= (int32_t)b->hs.size()) return nullptr;
+  return b->hs[i];
+}
+
+int cc_batch_sweep(cc_batch* b, int64_t k) {
+  if (!b) return bfail(nullptr, CC_ERR_ARG, "batch is NULL");
+  if (k < 0) return bfail(b, CC_ERR_ARG, "k must be >= 0");
+  for (size_t i = 0; i < b->hs.size(); ++i)
+    if (!b->active[i]) {
+      b->active.assign(b->hs.size(), 1);
+      b->stale[0] = b->stale[1] = true;
+      break;
+    }
+  return batch_sweep(b, k);
+}
+
+int cc_batch_solve(cc_batch* b, double tol, int64_t max_sweeps, int64_t* sweeps_done, int64_t* per_instance) {
+  if (!b) return bfail(nullptr, CC_ERR_ARG, "batch is NULL");
+  if (!std::isfinite(tol) || tol < 0 || max_sweeps < 0) return bfail(b, CC_ERR_ARG, "bad tol or max_sweeps");
+  const size_t m = b->hs.size();
+  b->active.assign(m, 1);
+  b->prev_fp32.assign(m, INFINITY);
+  b->stale[0] = b->stale[1] = true;
+  if (per_instance)
+    for (size_t i = 0; i < m; ++i) per_instance[i] = -1;
+  int64_t done = 0;
+  size_t left = m;
+  while (left > 0 && done < max_sweeps) {
+    const int64_t k = std::min<int64_t>(b->o.check_every, max_sweeps - done);
+    int rc = batch_sweep(b, k);
+    if (rc) return rc;
+    done += k;
+    // checks of all active instances, one synchronization
+    for (size_t i = 0; i < m; ++i)
+      if (b->active[i]) {
+        rc = check_launch(b->hs[i]);
+        if (rc) return bfail(b, rc, b->hs[i]->err);
+      }
+    BCK(b, cudaStreamSynchronize(b->st));
+    for (size_t i = 0; i < m; ++i) {
+      if (!b->active[i]) continue;
+      cc_handle* h = b->hs[i];
+      rc = read_ctl_error(h);
+      if (rc) return bfail(b, rc, "instance " + std::to_string(i) + ": " + h->err);
+      cc_stats s;
+      check_finish(h, &s);
+      if (h->fp32) {
+        const bool small = s.max_violation <= std::max(tol, b->o.refine_at);
+        const bool stalled = s.max_violation > 0.99 * b->prev_fp32[i];
+        b->prev_fp32[i] = s.max_violation;
+        if (!(small || stalled)) continue;
+        rc = switch_to_fp64(h);
+        if (rc) return bfail(b, rc, h->err);
+        b->stale[0] = b->stale[1] = true;
+        rc = cc_check(h, &s);
+        if (rc) return bfail(b, rc, h->err);
+      }
+      if (s.max_violation <= tol) {
+        b->active[i] = 0;
+        b->stale[0] = b->stale[1] = true;
+        --left;
+        if (per_instance) per_instance[i] = h->sweeps;
+      }
+    }
+  }
+  if (sweeps_done) *sweeps_done = done;
+  b->active.assign(m, 1);
+  b->stale[0] = b->stale[1] = true;
+  return left == 0 ? CC_OK : bfail(b, CC_ERR_NOT_CONVERGED, "max_sweeps reached before every instance converged");
+}
+
+int cc_batch_autotune(int32_t count, const int64_t* ns, const double* const* ds, const double* const* ws,
+                      const cc_opts* base, int32_t trial_sweeps, cc_opts* best, double* best_ms) {
+  if (!best || trial_sweeps < 1) return bfail(nullptr, CC_ERR_ARG, "best is NULL or trial_sweeps < 1");
+  cc_opts o;
+  cc_opts_default(&o);
+  if (base) o = *base;
+  const int tiles[3] = {8, 16, 32};
+  double best_t = INFINITY;
+  cc_opts pick = o;
+  for (int ti = 0; ti < 3; ++ti)
+    for (int order = 0; order < 2; ++order) {
+      cc_opts c = o;
+      c.tile = tiles[ti];
+      c.batch_order = order;
+      cc_batch* b = nullptr;
+      int rc = cc_batch_create(&b, count, ns, ds, ws, &c);
+      if (rc) return rc;
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      rc = cc_batch_sweep(b, trial_sweeps);                    // warm-up: the first sweeps are the busiest
+      if (!rc) {
+        cudaEventRecord(e0, b->st);
+        rc = cc_batch_sweep(b, trial_sweeps);
+        cudaEventRecord(e1, b->st);
+      }
+      float ms = 0;
+      if (!rc) {
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      std::string err = b->err;
+      cc_batch_destroy(b);
+      if (rc) return bfail(nullptr, rc, err);
+      const double per = ms / trial_sweeps;
+      if (per < best_t) {
+        best_t = per;
+        pick = c;
+      }
+    }
+  *best = pick;
+  if (best_ms) *best_ms = best_t;
+  return CC_OK;
+}
+
+const char* cc_batch_last_error(const cc_batch* b) {
+  if (!b) return g_create_error.c_str();
+  return b->err.c_str();
 }
 
 }  // extern "C"

@@ -51,6 +51,7 @@ struct TiledArgs {
   int* work;            // unused
   int nbt;              // block triples per sweep
   unsigned long long* trace;  // optional per-item timestamps (nullptr = off)
+  int* cnt;             // per-tile visit counters of this instance (batched sweep)
 };
 
 __device__ __forceinline__ void unpack_bt(int pk, int& I, int& J, int& K) {
@@ -759,6 +760,51 @@ __global__ void __launch_bounds__(NT) k_sweep_flow(TiledArgs<T> a, int* flow) {
       flow_pair_tile<T, B, NT>(a, tl);
     }
     first = false;
+    if (threadIdx.x == 0) sm.item = nxt;
+    __syncthreads();
+    w = sm.item;
+    __syncthreads();
+  }
+}
+
+// Many instances in one launch (the batched form).  `items` lists (instance,
+// local item) pairs; each instance's local items are its block triples in
+// schedule order, then its pair tiles, and the list keeps every instance's
+// items in that order, so each item depends only on items listed before it
+// and the dataflow argument above carries over.  Instances are independent,
+// so the items of one fill the dependency waits of another.
+template <typename T, bool UNITW, int B, int NT>
+__global__ void __launch_bounds__(NT) k_sweep_batch(const TiledArgs<T>* __restrict__ args,
+                                                    const int2* __restrict__ items, int total, int* next) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FlowSmem<T, B>& sm = *reinterpret_cast<FlowSmem<T, B>*>(smem_raw);
+  if (threadIdx.x == 0) sm.item = atomicAdd(next, 1);
+  __syncthreads();
+  int w = sm.item;
+  while (w < total) {
+    int nxt = 0;
+    if (threadIdx.x == 0) nxt = atomicAdd(next, 1);
+    const int2 it = items[w];
+    const TiledArgs<T>& a = args[it.x];
+    const int lw = it.y;
+    if (lw < a.nbt) {
+      int I, J, K;
+      unpack_bt(a.bt_list[lw], I, J, K);
+      const int g = (I + J + K) % a.nb;
+      const int64_t tIJ = tile_index(a.nb, I, J), tIK = tile_index(a.nb, I, K), tJK = tile_index(a.nb, J, K);
+      const int64_t u1 = (K == J) ? -1 : tIK, u2 = (I == J) ? -1 : tJK;
+      if (threadIdx.x == 0) sm.flag = wait_tiles(a.cnt, tIJ, u1, u2, g, a.ctl, a.timeout_ns, g);
+      __syncthreads();
+      if (!sm.flag) return;
+      flow_block_triple<T, UNITW, B, NT>(a, lw, I, J, K, sm);
+      if (threadIdx.x == 0) release_tiles(a.cnt, tIJ, u1, u2);
+    } else {
+      const int tl = lw - a.nbt;
+      if (threadIdx.x == 0) sm.flag = wait_tiles(a.cnt, tl, -1, -1, a.nb, a.ctl, a.timeout_ns, a.nb);
+      __syncthreads();
+      if (!sm.flag) return;
+      flow_pair_tile<T, B, NT>(a, tl);
+    }
     if (threadIdx.x == 0) sm.item = nxt;
     __syncthreads();
     w = sm.item;
