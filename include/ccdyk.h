@@ -230,7 +230,7 @@ int cc_check_noalloc(int64_t n, double eps, const double* x, const double* f, co
                      const double* w, const double* y_pair, double* out, void* stream);
 
 /* ---- batches: many instances of uneven size, one launch per sweep -------
- * Survey row "batched form"; the paper has one instance per run.  A batch
+ * Not in the paper, which solves one instance per run.  A batch
  * owns one handle per instance (all with the same options: tiled schedule,
  * fused form, same tile and precision); every sweep of the batch is one
  * cooperative launch that drains a single work list holding the block
@@ -277,6 +277,66 @@ void cc_batch_destroy(cc_batch* b);
 
 /* Message of the last failed call on b (NULL: of the last failed create). */
 const char* cc_batch_last_error(const cc_batch* b);
+
+/* ---- learned dual warm start (not in the paper) -------------------------
+ * Dykstra's method on this QP is Hildreth's method (Sec. II-B, Algorithm 1),
+ * i.e. coordinate ascent on the dual, so it converges to the same optimum
+ * from any nonnegative dual start, provided the primal iterate is rebuilt
+ * from those duals through x = x0 - W^{-1} A^T y / eps, the relation that
+ * every correction and projection step of Algorithm 1 preserves.
+ * A small MLP proposes such a start.
+ *   Candidates: triplets (i, j, k) with at least one edge (d = 0) among
+ *     their three pairs; all other triangle duals and all pair duals start
+ *     at 0.
+ *   Features (5 floats, row stride CC_WS_FEAT): d_ij, d_ik, d_jk,
+ *     log(1 + (deg i + deg j + deg k) / mean degree),
+ *     log(1 + number of objects adjacent to all three); degrees count edges.
+ *   Network: 5 -> 64 -> 64 -> 3, ReLU, softplus output = the triplet's three
+ *     duals y; BF16 weights and activations, FP32 accumulation, on the
+ *     tensor cores (mma.sync m16n8k16).
+ *   Parameters: CC_WS_NPARAM floats, W1[5][64], b1[64], W2[64][64], b2[64],
+ *     W3[64][3], b3[3] (row-major [in][out]; y = x W + b).
+ * Rows of the three outputs follow the handle's internal triplet order; a
+ * network is trained on samples of that same order (cc_ws_samples). */
+#define CC_WS_NPARAM 4739
+#define CC_WS_FEAT 8
+
+/* Replace the handle's duals by the network's prediction (host params),
+ * outputs below `threshold` set to 0, pair duals 0, rebuild x and f from
+ * them in FP64 and reset the sweep count.  *candidates (nullable): the
+ * number of candidate triplets.  Needs the tiled schedule, fused form and an
+ * FP64 state (CC_ERR_UNSUPPORTED otherwise).  Synchronous.  Errors:
+ * CC_ERR_ARG, CC_ERR_UNSUPPORTED, CC_ERR_OOM, CC_ERR_CUDA. */
+int cc_warm_start_mlp(cc_handle* h, const float* params, double threshold, int64_t* candidates);
+
+/* Training samples of the handle's current state: feat (device, cap rows of
+ * CC_WS_FEAT floats) and target (device, cap rows of 3 floats: the current
+ * triangle duals y of each candidate).  *count receives the number of
+ * candidates; with feat and target NULL only the count is computed.
+ * CC_ERR_ARG when cap < count (nothing written).  Synchronous; same
+ * requirements as cc_warm_start_mlp. */
+int cc_ws_samples(cc_handle* h, float* feat, float* target, int64_t cap, int64_t* count);
+
+/* out[3q + r] = output r of the network (host params) on feature row q of
+ * feat (device, count rows of CC_WS_FEAT floats); out is device memory.
+ * Synchronous on `stream` (cudaStream_t; NULL = legacy default stream). */
+int cc_mlp_forward(const float* params, const float* feat, float* out, int64_t count, void* stream);
+
+/* Gradient of the mean squared error L = sum_q sum_r (out[q][r] - target[q][r])^2
+ * / (3 count) over all count rows (feat, target: device; params, grad
+ * (CC_WS_NPARAM floats), loss (nullable): host).  Same arithmetic as one
+ * training step (BF16 operands, FP32 accumulation).  Synchronous. */
+int cc_mlp_grad(const float* params, const float* feat, const float* target, int64_t count, float* grad, float* loss,
+                void* stream);
+
+/* `steps` Adam steps (beta 0.9 / 0.999, eps 1e-8, learning rate lr, FP32
+ * master weights) on minibatches of `batch` rows drawn uniformly with
+ * replacement (SplitMix64 of seed, step and row) from the count rows of
+ * feat / target (device).  params (host) holds the initial weights and
+ * receives the trained ones; loss (host, nullable): `steps` floats, the
+ * minibatch loss before each step.  Synchronous. */
+int cc_mlp_train(float* params, const float* feat, const float* target, int64_t count, int32_t batch, int32_t steps,
+                 float lr, uint64_t seed, float* loss, void* stream);
 
 /* Release everything the handle owns.  NULL is a no-op. */
 void cc_destroy(cc_handle* h);

@@ -160,6 +160,11 @@ class Solver:
     def device_bytes(self) -> int:
         return cc_device_bytes(self.h)
 
+    def warm_start(self, params, threshold: float = 0.0) -> int:
+        """Start from the duals a trained warm-start network predicts (see
+        ``warmstart``); returns the number of candidate triplets."""
+        return _native.cc_warm_start_mlp(self.h, params, threshold)
+
     @classmethod
     def _borrow(cls, h, n, eps):
         """A view of a handle owned elsewhere (an instance of a Batch)."""

@@ -79,7 +79,11 @@ EXPORTS = ("cc_opts_default", "cc_create", "cc_create_device", "cc_sweep", "cc_c
            "cc_device_bytes", "cc_destroy", "cc_last_error", "cc_check_noalloc",
            "cc_refine_fp64", "cc_set_duals", "cc_get_trace", "cc_batch_create", "cc_batch_size",
            "cc_batch_handle", "cc_batch_sweep", "cc_batch_solve", "cc_batch_autotune", "cc_batch_destroy",
-           "cc_batch_last_error")
+           "cc_batch_last_error", "cc_warm_start_mlp", "cc_ws_samples", "cc_mlp_forward", "cc_mlp_grad",
+           "cc_mlp_train")
+
+CC_WS_NPARAM = 4739
+CC_WS_FEAT = 8
 
 _lib = None
 _lock = threading.Lock()
@@ -159,6 +163,18 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         vp = ctypes.c_void_p
         lib.cc_check_noalloc.argtypes = [i64, ctypes.c_double, vp, vp, vp, vp, vp, vp, vp]
         lib.cc_check_noalloc.restype = ctypes.c_int
+        fp = ctypes.POINTER(ctypes.c_float)
+        lib.cc_warm_start_mlp.argtypes = [H, fp, ctypes.c_double, I64P]
+        lib.cc_warm_start_mlp.restype = ctypes.c_int
+        lib.cc_ws_samples.argtypes = [H, vp, vp, i64, I64P]
+        lib.cc_ws_samples.restype = ctypes.c_int
+        lib.cc_mlp_forward.argtypes = [fp, vp, vp, i64, vp]
+        lib.cc_mlp_forward.restype = ctypes.c_int
+        lib.cc_mlp_grad.argtypes = [fp, vp, vp, i64, fp, fp, vp]
+        lib.cc_mlp_grad.restype = ctypes.c_int
+        lib.cc_mlp_train.argtypes = [fp, vp, vp, i64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                     ctypes.c_uint64, fp, vp]
+        lib.cc_mlp_train.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -352,3 +368,67 @@ def cc_batch_destroy(b) -> None:
 def cc_batch_last_error(b=None) -> str:
     m = load().cc_batch_last_error(b)
     return m.decode() if m else ""
+
+
+# ---- learned dual warm start -------------------------------------------------
+
+def _fp(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _params(p):
+    import numpy as np
+    a = np.ascontiguousarray(p, dtype=np.float32)
+    if a.shape != (CC_WS_NPARAM,):
+        raise ValueError(f"params must hold {CC_WS_NPARAM} floats")
+    return a
+
+
+def cc_warm_start_mlp(h, params, threshold: float) -> int:
+    """Replace the duals by the network's prediction; returns the number of
+    candidate triplets."""
+    p = _params(params)
+    cand = ctypes.c_int64(0)
+    _check(load().cc_warm_start_mlp(h, _fp(p), threshold, ctypes.byref(cand)), h)
+    return cand.value
+
+
+def cc_ws_samples(h, feat_ptr: int = 0, target_ptr: int = 0, cap: int = 0) -> int:
+    """Candidate count; with device pointers also writes features and targets."""
+    cnt = ctypes.c_int64(0)
+    v = ctypes.c_void_p
+    _check(load().cc_ws_samples(h, v(feat_ptr) if feat_ptr else None, v(target_ptr) if target_ptr else None,
+                                cap, ctypes.byref(cnt)), h)
+    return cnt.value
+
+
+def cc_mlp_forward(params, feat_ptr: int, out_ptr: int, count: int, stream: int = 0) -> None:
+    p = _params(params)
+    v = ctypes.c_void_p
+    _check(load().cc_mlp_forward(_fp(p), v(feat_ptr), v(out_ptr), count, v(stream)), None)
+
+
+def cc_mlp_grad(params, feat_ptr: int, target_ptr: int, count: int, stream: int = 0):
+    """Returns (gradient as float32 array, loss)."""
+    import numpy as np
+    p = _params(params)
+    g = np.zeros(CC_WS_NPARAM, dtype=np.float32)
+    loss = ctypes.c_float(0.0)
+    v = ctypes.c_void_p
+    _check(load().cc_mlp_grad(_fp(p), v(feat_ptr), v(target_ptr), count, _fp(g), ctypes.byref(loss), v(stream)),
+           None)
+    return g, float(loss.value)
+
+
+def cc_mlp_train(params, feat_ptr: int, target_ptr: int, count: int, batch: int, steps: int, lr: float,
+                 seed: int, stream: int = 0):
+    """Returns (trained params, per-step minibatch losses); params is not modified."""
+    import numpy as np
+    p = _params(params).copy()
+    losses = np.zeros(max(steps, 0), dtype=np.float32)
+    v = ctypes.c_void_p
+    _check(load().cc_mlp_train(_fp(p), v(feat_ptr), v(target_ptr), count, batch, steps, lr, seed,
+                               _fp(losses) if steps > 0 else None, v(stream)), None)
+    return p, losses

@@ -1,5 +1,6 @@
 // C ABI of the GPU Dykstra solver (declared in include/ccdyk.h): handle
 // state, device memory, schedule tables and kernel launches.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -13,6 +14,7 @@
 #include "common.cuh"
 #include "tiled.cuh"
 #include "listsched.cuh"
+#include "warmstart.cuh"
 
 using namespace ccd;
 
@@ -1425,6 +1427,250 @@ int cc_batch_autotune(int32_t count, const int64_t* ns, const double* const* ds,
 const char* cc_batch_last_error(const cc_batch* b) {
   if (!b) return g_create_error.c_str();
   return b->err.c_str();
+}
+
+}  // extern "C"
+
+// ====================================================================== warm start
+
+namespace {
+
+// Candidates (triplets with an edge), their features, and the adjacency the
+// features come from; device buffers owned by the caller of this helper.
+struct WsCands {
+  int64_t* cand = nullptr;
+  float* feat = nullptr;
+  int64_t count = 0;
+};
+
+int ws_build(cc_handle* h, WsCands& c, bool features) {
+  const int n = (int)h->n, words = (n + 31) / 32;
+  uint32_t* adj = (uint32_t*)dalloc(h, (size_t)n * words * sizeof(uint32_t));
+  int* deg = (int*)dalloc(h, (size_t)n * sizeof(int));
+  int* cnt = (int*)dalloc(h, (size_t)h->P * sizeof(int));
+  int64_t* off = (int64_t*)dalloc(h, (size_t)h->P * sizeof(int64_t));
+  auto cleanup = [&]() { dfree(h, adj); dfree(h, deg); dfree(h, cnt); dfree(h, off); };
+  if (!adj || !deg || !cnt || !off) {
+    cleanup();
+    return fail(h, CC_ERR_OOM, "warm-start buffers");
+  }
+  CK(h, cudaMemsetAsync(adj, 0, (size_t)n * words * sizeof(uint32_t), h->st));
+  k_ws_adjacency<<<grid_for(h, h->tile_elems, 256), 256, 0, h->st>>>(h->d64, h->tile_list, h->ntiles, n, h->B, adj, words);
+  k_ws_degree<<<grid_for(h, n, 256), 256, 0, h->st>>>(adj, n, words, deg);
+  k_ws_candidates<<<grid_for(h, h->P, 256), 256, 0, h->st>>>(adj, n, words, 0, cnt, nullptr, nullptr);
+  CK(h, cudaGetLastError());
+  std::vector<int> hc((size_t)h->P), hd(n);
+  CK(h, cudaMemcpyAsync(hc.data(), cnt, (size_t)h->P * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaMemcpyAsync(hd.data(), deg, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  std::vector<int64_t> ho((size_t)h->P);
+  int64_t total = 0;
+  for (int64_t p = 0; p < h->P; ++p) {
+    ho[p] = total;
+    total += hc[p];
+  }
+  int64_t degsum = 0;
+  for (int v : hd) degsum += v;
+  const float inv_mean = degsum > 0 ? (float)((double)n / (double)degsum) : 0.f;
+  c.count = total;
+  c.cand = (int64_t*)dalloc(h, (size_t)std::max<int64_t>(total, 1) * sizeof(int64_t));
+  if (features) c.feat = (float*)dalloc(h, (size_t)std::max<int64_t>(total, 1) * WS_FEAT * sizeof(float));
+  if (!c.cand || (features && !c.feat)) {
+    cleanup();
+    return fail(h, CC_ERR_OOM, "warm-start candidates");
+  }
+  CK(h, cudaMemcpyAsync(off, ho.data(), (size_t)h->P * sizeof(int64_t), cudaMemcpyHostToDevice, h->st));
+  k_ws_candidates<<<grid_for(h, h->P, 256), 256, 0, h->st>>>(adj, n, words, 1, nullptr, off, c.cand);
+  if (features && total > 0)
+    k_ws_features<<<grid_for(h, total, 256), 256, 0, h->st>>>(c.cand, total, h->d64, adj, deg, n, h->nb, h->B, words,
+                                                              inv_mean, c.feat);
+  CK(h, cudaGetLastError());
+  CK(h, cudaStreamSynchronize(h->st));
+  cleanup();
+  return CC_OK;
+}
+
+void ws_release(cc_handle* h, WsCands& c) {
+  dfree(h, c.cand);
+  dfree(h, c.feat);
+  c.cand = nullptr;
+  c.feat = nullptr;
+}
+
+bool ws_usable(const cc_handle* h) {
+  return h->o.schedule == CC_SCHED_TILED && !h->o.exact && !h->fp32 && h->mask;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cc_warm_start_mlp(cc_handle* h, const float* params, double threshold, int64_t* candidates) {
+  if (!h) return fail(nullptr, CC_ERR_ARG, "handle is NULL");
+  if (!params) return fail(h, CC_ERR_ARG, "params is NULL");
+  if (!ws_usable(h)) return fail(h, CC_ERR_UNSUPPORTED, "warm start needs the tiled schedule, fused form, FP64 state");
+  CK(h, cudaSetDevice(h->dev));
+  int rc = read_ctl_error(h);
+  if (rc) return rc;
+  WsCands c;
+  rc = ws_build(h, c, true);
+  if (rc) return rc;
+  float* pd = (float*)dalloc(h, WS_NPARAM * sizeof(float));
+  if (!pd) {
+    ws_release(h, c);
+    return fail(h, CC_ERR_OOM, "parameters");
+  }
+  CK(h, cudaMemcpyAsync(pd, params, WS_NPARAM * sizeof(float), cudaMemcpyHostToDevice, h->st));
+  CK(h, cudaMemsetAsync(h->zt, 0, (size_t)h->zt_elems * sizeof(double), h->st));
+  CK(h, cudaMemsetAsync(h->zp, 0, (size_t)h->tile_elems * 2 * sizeof(double), h->st));
+  if (c.count > 0) {
+    const int grid = (int)std::min<int64_t>((c.count + 127) / 128, (int64_t)h->sms * 8);
+    k_ws_infer<<<grid, 256, 0, h->st>>>(pd, c.feat, c.count, 1, nullptr, c.cand, (double*)h->zt, h->bt_rank, h->nb,
+                                        h->B, h->o.eps, (float)threshold);
+  }
+  CK(h, cudaGetLastError());
+  const int g2 = grid_for(h, h->mask_words, 256);
+  if (h->B == 8) k_rebuild_mask<double, 8><<<g2, 256, 0, h->st>>>((const double*)h->zt, h->mask, h->mask_words);
+  else if (h->B == 16) k_rebuild_mask<double, 16><<<g2, 256, 0, h->st>>>((const double*)h->zt, h->mask, h->mask_words);
+  else k_rebuild_mask<double, 32><<<g2, 256, 0, h->st>>>((const double*)h->zt, h->mask, h->mask_words);
+  CK(h, cudaGetLastError());
+  rc = resync_fp64(h);
+  CK(h, cudaStreamSynchronize(h->st));
+  dfree(h, pd);
+  ws_release(h, c);
+  if (rc) return rc;
+  h->sweeps = 0;
+  h->fp32_sweeps = 0;
+  if (candidates) *candidates = c.count;
+  return CC_OK;
+}
+
+int cc_ws_samples(cc_handle* h, float* feat, float* target, int64_t cap, int64_t* count) {
+  if (!h || !count) return fail(h, CC_ERR_ARG, "handle or count is NULL");
+  if (!ws_usable(h)) return fail(h, CC_ERR_UNSUPPORTED, "samples need the tiled schedule, fused form, FP64 state");
+  CK(h, cudaSetDevice(h->dev));
+  int rc = read_ctl_error(h);
+  if (rc) return rc;
+  WsCands c;
+  rc = ws_build(h, c, true);
+  if (rc) return rc;
+  *count = c.count;
+  if (feat && target && c.count <= cap && c.count > 0) {
+    CK(h, cudaMemcpyAsync(feat, c.feat, (size_t)c.count * WS_FEAT * sizeof(float), cudaMemcpyDeviceToDevice, h->st));
+    k_ws_targets<<<grid_for(h, c.count, 256), 256, 0, h->st>>>(c.cand, c.count, (const double*)h->zt, h->bt_rank,
+                                                               h->nb, h->B, h->o.eps, target);
+    CK(h, cudaGetLastError());
+  }
+  CK(h, cudaStreamSynchronize(h->st));
+  ws_release(h, c);
+  if ((feat || target) && c.count > cap) return fail(h, CC_ERR_ARG, "cap is smaller than the sample count");
+  return CC_OK;
+}
+
+int cc_mlp_forward(const float* params, const float* feat, float* out, int64_t count, void* stream) {
+  if (!params || !feat || !out || count < 0) return fail(nullptr, CC_ERR_ARG, "NULL argument or count < 0");
+  if (count == 0) return CC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  float* pd = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&pd, WS_NPARAM * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pd, params, WS_NPARAM * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    int sms = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)std::min<int64_t>((count + 127) / 128, (int64_t)sms * 8);
+    k_ws_infer<<<grid, 256, 0, st>>>(pd, feat, count, 0, out, nullptr, nullptr, nullptr, 0, 8, 1.0, 0.f);
+    e = cudaGetLastError();
+  }
+  if (pd) cudaFreeAsync(pd, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(nullptr, CC_ERR_CUDA, std::string("cc_mlp_forward: ") + cudaGetErrorString(e));
+  return CC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Device copies of the parameters, Adam moments, gradient and per-step loss.
+struct WsTrainBufs {
+  float* p = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  float* g = nullptr;
+  float* loss = nullptr;
+};
+
+cudaError_t ws_train_alloc(WsTrainBufs& b, int steps, cudaStream_t st) {
+  const size_t np = WS_NPARAM * sizeof(float);
+  cudaError_t e = cudaMallocAsync((void**)&b.p, 4 * np + (size_t)std::max(steps, 1) * sizeof(float), st);
+  if (e != cudaSuccess) return e;
+  b.m = b.p + WS_NPARAM;
+  b.v = b.m + WS_NPARAM;
+  b.g = b.v + WS_NPARAM;
+  b.loss = b.g + WS_NPARAM;
+  return cudaMemsetAsync(b.m, 0, 3 * np + (size_t)std::max(steps, 1) * sizeof(float), st);
+}
+
+cudaError_t ws_train_launch(const WsTrainBufs& b, const float* feat, const float* target, int64_t count, int64_t rows,
+                            int sample, uint64_t seed, float* loss, cudaStream_t st) {
+  const size_t smem = sizeof(WsTrainSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_ws_train_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t chunks = (rows + 15) / 16;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((chunks + WS_TRAIN_WARPS - 1) / WS_TRAIN_WARPS, sms));
+  k_ws_train_grad<<<grid, 32 * WS_TRAIN_WARPS, smem, st>>>(b.p, feat, target, count, rows, sample, seed, b.g, loss);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+int cc_mlp_grad(const float* params, const float* feat, const float* target, int64_t count, float* grad, float* loss,
+                void* stream) {
+  if (!params || !feat || !target || !grad || count <= 0) return fail(nullptr, CC_ERR_ARG, "NULL argument or count <= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  WsTrainBufs b;
+  cudaError_t e = ws_train_alloc(b, 1, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b.p, params, WS_NPARAM * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = ws_train_launch(b, feat, target, count, count, 0, 0, b.loss, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(grad, b.g, WS_NPARAM * sizeof(float), cudaMemcpyDeviceToHost, st);
+  float l = 0.f;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&l, b.loss, sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (b.p) cudaFreeAsync(b.p, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(nullptr, CC_ERR_CUDA, std::string("cc_mlp_grad: ") + cudaGetErrorString(e));
+  if (loss) *loss = l;
+  return CC_OK;
+}
+
+int cc_mlp_train(float* params, const float* feat, const float* target, int64_t count, int32_t batch, int32_t steps,
+                 float lr, uint64_t seed, float* loss, void* stream) {
+  if (!params || !feat || !target || count <= 0 || batch <= 0 || steps < 0 || !(lr > 0.f))
+    return fail(nullptr, CC_ERR_ARG, "NULL argument, count/batch <= 0, steps < 0 or lr <= 0");
+  if (steps == 0) return CC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  WsTrainBufs b;
+  cudaError_t e = ws_train_alloc(b, steps, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b.p, params, WS_NPARAM * sizeof(float), cudaMemcpyHostToDevice, st);
+  for (int s = 0; s < steps && e == cudaSuccess; ++s) {
+    e = ws_train_launch(b, feat, target, count, batch, 1, seed * 1000003ull + (uint64_t)s, b.loss + s, st);
+    if (e == cudaSuccess) {
+      k_ws_adam<<<(WS_NPARAM + 255) / 256, 256, 0, st>>>(b.p, b.m, b.v, b.g, lr, 0.9f, 0.999f, 1e-8f, s + 1);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(params, b.p, WS_NPARAM * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, b.loss, (size_t)steps * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (b.p) cudaFreeAsync(b.p, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(nullptr, CC_ERR_CUDA, std::string("cc_mlp_train: ") + cudaGetErrorString(e));
+  return CC_OK;
 }
 
 }  // extern "C"

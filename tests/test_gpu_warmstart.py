@@ -1,0 +1,212 @@
+"""Learned dual warm start (GPU, through the C ABI): features and targets,
+the tensor-core MLP forward and gradient against a plain PyTorch fp32
+reference with the same BF16 operand rounding, training, and warm-started
+solves that reach the cold-start optimum (Dykstra/Hildreth, Sec. II-B,
+converges to the unique QP solution from any nonnegative dual start)."""
+import numpy as np
+import pytest
+
+import oracle
+from instances import chung_lu, planted_partition
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _solver(n, d, w, **kw):
+    import paper_1901_10084_gb300 as cc
+    kw.setdefault("interleave", False)
+    return cc.Solver(n, d, w, **kw)
+
+
+def _bf(t):
+    torch = _torch()
+    return t.to(torch.bfloat16).to(torch.float32)
+
+
+def _reference_forward(params, feat):
+    """Plain fp32 MLP with BF16-rounded weights, inputs and hidden
+    activations (the operands the tensor cores see); biases stay fp32."""
+    torch = _torch()
+    from paper_1901_10084_gb300.warmstart import unpack
+    W1, b1, W2, b2, W3, b3 = [torch.tensor(a) for a in unpack(params)]
+    x = _bf(feat[:, :5])
+    h1 = x @ _bf(W1) + b1
+    h2 = _bf(torch.relu(h1)) @ _bf(W2) + b2
+    o = _bf(torch.relu(h2)) @ _bf(W3) + b3
+    return torch.nn.functional.softplus(o)
+
+
+def _features_numpy(n, d):
+    """Candidates and features in packed (a, b) order, c ascending, from d."""
+    D = np.zeros((n, n))
+    iu, ju = np.triu_indices(n, 1)
+    D[iu, ju] = d
+    D = D + D.T
+    A = (D == 0.0) & ~np.eye(n, dtype=bool)
+    deg = A.sum(1)
+    mean = deg.sum() / n
+    rows, trip = [], []
+    for a, b in zip(iu, ju):
+        for c in range(b + 1, n):
+            if A[a, b] or A[a, c] or A[b, c]:
+                common = int(np.sum(A[a] & A[b] & A[c]))
+                rows.append([D[a, b], D[a, c], D[b, c], np.log1p((deg[a] + deg[b] + deg[c]) / mean),
+                             np.log1p(common)])
+                trip.append((a, b, c))
+    return np.array(rows, dtype=np.float64).reshape(-1, 5), trip
+
+
+@pytest.mark.parametrize("n,tile", [(60, 16), (75, 8)])
+def test_features_and_targets_match_a_numpy_recount(n, tile):
+    from paper_1901_10084_gb300 import warmstart
+    d, w, _ = planted_partition(n, 4, 0.6, 0.1, seed=n)
+    ref, trip = _features_numpy(n, d)
+    with _solver(n, d, w, tile=tile) as s:
+        s.sweep(9)
+        feat, targ = warmstart.samples(s)
+        yt, _ = s.get_duals()
+    feat = feat.cpu().numpy()
+    targ = targ.cpu().numpy()
+    assert feat.shape[0] == len(trip)
+    np.testing.assert_allclose(feat[:, :5], ref, rtol=1e-6, atol=1e-6)
+    assert np.all(feat[:, 5:] == 0)
+    idx = np.array([oracle.trank(n, a, b, c) for a, b, c in trip])
+    expect = yt.reshape(-1, 3)[idx]
+    np.testing.assert_allclose(targ, expect, rtol=1e-6, atol=1e-30)
+
+
+def _sample_features(count, seed):
+    rng = np.random.default_rng(seed)
+    f = np.zeros((count, 8), dtype=np.float32)
+    f[:, :3] = rng.integers(0, 2, (count, 3))
+    f[:, 3] = rng.uniform(0.3, 3.0, count)
+    f[:, 4] = rng.uniform(0.0, 3.0, count)
+    return f
+
+
+@pytest.mark.parametrize("count", [1, 15, 16, 1000, 4099])
+def test_forward_matches_fp32_reference(count):
+    torch = _torch()
+    from paper_1901_10084_gb300 import warmstart
+    params = warmstart.init_params(seed=count, out_bias=0.0)
+    feat = torch.tensor(_sample_features(count, count))
+    out = warmstart.forward(params, feat.cuda()).cpu()
+    ref = _reference_forward(params, feat)
+    torch.testing.assert_close(out, ref, rtol=2e-2, atol=2e-3)
+
+
+def test_forward_of_empty_input():
+    torch = _torch()
+    from paper_1901_10084_gb300 import warmstart
+    out = warmstart.forward(warmstart.init_params(0), torch.zeros((0, 8), device="cuda"))
+    assert out.shape == (0, 3)
+
+
+@pytest.mark.parametrize("count", [16, 333, 2048])
+def test_gradient_matches_fp32_autograd(count):
+    torch = _torch()
+    from paper_1901_10084_gb300 import warmstart
+    params = warmstart.init_params(seed=7, out_bias=-0.5)
+    feat = torch.tensor(_sample_features(count, 100 + count))
+    target = torch.tensor(np.random.default_rng(count).exponential(0.3, (count, 3)).astype(np.float32))
+    g, loss = warmstart.grad(params, feat.cuda(), target.cuda())
+    p = torch.tensor(params, requires_grad=True)
+    parts, o = [], 0
+    for size in (5 * 64, 64, 64 * 64, 64, 64 * 3, 3):
+        parts.append(p[o:o + size])
+        o += size
+    W1, b1, W2, b2, W3, b3 = (parts[0].view(5, 64), parts[1], parts[2].view(64, 64), parts[3],
+                              parts[4].view(64, 3), parts[5])
+    x = _bf(feat[:, :5])
+    h1 = x @ W1 + b1
+    h2 = torch.relu(h1) @ W2 + b2
+    out = torch.nn.functional.softplus(torch.relu(h2) @ W3 + b3)
+    ref_loss = ((out - target) ** 2).mean()
+    ref_loss.backward()
+    gref = p.grad.numpy()
+    assert abs(loss - ref_loss.item()) <= 2e-2 * ref_loss.item()
+    o = 0
+    for size in (5 * 64, 64, 64 * 64, 64, 64 * 3, 3):
+        a, b = g[o:o + size], gref[o:o + size]
+        assert np.linalg.norm(a - b) <= 5e-2 * np.linalg.norm(b) + 1e-7, (o, size)
+        o += size
+
+
+def test_training_lowers_the_loss_on_solver_duals():
+    from paper_1901_10084_gb300 import warmstart
+    inst = [chung_lu(150, 2.5, 8.0, seed=s)[:2] for s in (11, 12)]
+    feat, targ, sweeps = warmstart.collect([(150, d, w) for d, w in inst], tol=1e-4)
+    assert all(k > 0 for k in sweeps)
+    p0 = warmstart.init_params(3)
+    _, l0 = warmstart.grad(p0, feat, targ)
+    params, losses = warmstart.train(feat, targ, steps=400, batch=2048, lr=3e-3, seed=3, params=p0)
+    _, l1 = warmstart.grad(params, feat, targ)
+    assert np.all(np.isfinite(losses))
+    assert l1 < 0.5 * l0
+    assert losses[-20:].mean() < losses[:20].mean()
+
+
+def _trained(seed=5):
+    from paper_1901_10084_gb300 import warmstart
+    inst = [chung_lu(150, 2.5, 8.0, seed=s)[:2] for s in (21, 22)]
+    feat, targ, _ = warmstart.collect([(150, d, w) for d, w in inst], tol=1e-4)
+    params, _ = warmstart.train(feat, targ, steps=300, batch=2048, lr=3e-3, seed=seed)
+    return params
+
+
+@pytest.mark.parametrize("interleave", [False, True])
+def test_warm_started_solve_reaches_the_cold_optimum(interleave):
+    params = _trained()
+    n = 200
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=40)
+    res = {}
+    for mode in ("cold", "warm"):
+        with _solver(n, d, w, tile=16, interleave=interleave, check_every=5) as s:
+            if mode == "warm":
+                cand = s.warm_start(params, threshold=1e-3)
+                assert cand > 0
+                yt, yp = s.get_duals()
+                assert yt.min() >= 0.0 and np.all(yp == 0.0)
+                x, f = s.get_x()
+                from oracle.dense import invariant_residual
+                assert invariant_residual(n, d, w, 0.2, x, f, yt, yp) <= 1e-12
+            ok, k = s.solve(1e-7, 20000)
+            assert ok
+            res[mode] = (s.check(), s.get_x()[0])
+    (c0, x0), (c1, x1) = res["cold"], res["warm"]
+    assert abs(c1["lp_objective"] - c0["lp_objective"]) <= 1e-5 * abs(c0["lp_objective"])
+    assert np.max(np.abs(x1 - x0)) <= 1e-4
+
+
+def test_zero_prediction_is_the_cold_start_bitwise():
+    """Threshold above every output: all duals 0, so the rebuilt state is
+    x0 and the following sweeps match a fresh solver bit for bit."""
+    from paper_1901_10084_gb300 import warmstart
+    n = 90
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=9, weights=(0.5, 2.0))
+    params = warmstart.init_params(1)
+    with _solver(n, d, w, tile=16) as a, _solver(n, d, w, tile=16) as b:
+        a.sweep(4)
+        a.warm_start(params, threshold=1e30)
+        a.sweep(3)
+        b.sweep(3)
+        xa, fa = a.get_x()
+        xb, fb = b.get_x()
+        assert np.array_equal(xa, xb) and np.array_equal(fa, fb)
+        assert a.stats()["sweeps"] == 3
+
+
+def test_warm_start_rejects_the_exact_form():
+    import paper_1901_10084_gb300 as cc
+    from paper_1901_10084_gb300 import warmstart
+    n = 40
+    d, w, _ = planted_partition(n, 2, 0.7, 0.1, seed=1)
+    with _solver(n, d, w, tile=8, exact=True) as s:
+        with pytest.raises(cc.CCError) as e:
+            s.warm_start(warmstart.init_params(0))
+        assert e.value.code == cc.CC_ERR_UNSUPPORTED
