@@ -55,6 +55,11 @@ def parse():
                    help="skip the FP32 bulk + FP64 refinement time-to-tolerance solve")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
     p.add_argument("--batch-count", type=int, default=256)
+    p.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start measurement")
+    p.add_argument("--ws-train-count", type=int, default=2000,
+                   help="Chung-Lu n=200 training instances for the warm-start network")
+    p.add_argument("--ws-steps", type=int, default=3000)
+    p.add_argument("--ws-threshold", type=float, default=1e-2)
     return p.parse_args()
 
 
@@ -245,6 +250,8 @@ def run_ours(args, rank, world, local_rank):
             out["precision_form"] = pf
     if rank == 0 and not args.no_batch and args.schedule == "tiled":
         out["batched_form"] = _batched(args, stream)
+    if rank == 0 and not args.no_warm_start and args.schedule == "tiled":
+        out["warm_start"] = _warm_start(args, stream)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -298,6 +305,56 @@ def _batched(args, stream):
     one = (time.perf_counter() - t) / len(sample)
     rec["sequential_estimate"] = {"seconds": one * len(inst), "sample": len(sample),
                                   "note": "mean single-instance FP64 solve time of the sample x instances"}
+    return rec
+
+
+def _warm_start(args, stream):
+    """Learned dual warm start: solve `ws_train_count` Chung-Lu n=200
+    instances (exponent 2.5, mean degree 8, seeds 400000+i) to the tolerance
+    as batches, train the network on their duals, then solve Chung-Lu
+    n=1000 (seed 1) and n=2000 (seed 4) from the cold start and from the
+    predicted duals.  Warm wall time includes features, inference and the
+    resync."""
+    import numpy as np
+    import torch
+
+    import paper_1901_10084_gb300 as cc
+    from paper_1901_10084_gb300 import warmstart
+    from instances import chung_lu
+    inst = [(200,) + tuple(chung_lu(200, 2.5, 8.0, seed=400000 + i)[:2]) for i in range(args.ws_train_count)]
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    feat, targ, sw = warmstart.collect_batch(inst, tol=args.tol)
+    torch.cuda.synchronize()
+    rec = {"train_instances": len(inst), "collect_seconds": time.perf_counter() - t,
+           "samples": int(feat.shape[0]), "unconverged": int(sum(1 for k in sw if k < 0)),
+           "threshold": args.ws_threshold, "tol": args.tol}
+    t = time.perf_counter()
+    params, losses = warmstart.train(feat, targ, steps=args.ws_steps, batch=8192, lr=3e-3, seed=1)
+    torch.cuda.synchronize()
+    rec["train_seconds"] = time.perf_counter() - t
+    rec["train_steps"] = args.ws_steps
+    _, rec["loss"] = warmstart.grad(params, feat, targ)
+    rec["loss_zero_prediction"] = float((targ.double() ** 2).mean())
+    del feat, targ
+    torch.cuda.empty_cache()
+    for name, n, seed in (("chunglu1000", 1000, 1), ("chunglu2000", 2000, 4)):
+        d, w, _ = chung_lu(n, 2.5, 8.0, seed=seed)
+        r = {}
+        for mode in ("cold", "warm"):
+            with cc.Solver(n, d, w, tile=args.tile, check_every=5, stream=stream) as s:
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                if mode == "warm":
+                    r["candidates"] = s.warm_start(params, args.ws_threshold)
+                    torch.cuda.synchronize()
+                    r["warm_start_seconds"] = time.perf_counter() - t
+                ok, k = s.solve(args.tol, args.ttt_max_sweeps)
+                torch.cuda.synchronize()
+                r[mode] = {"seconds": time.perf_counter() - t, "sweeps": k, "converged": ok,
+                           "lp_objective": s.check()["lp_objective"]}
+        r["speedup"] = r["cold"]["seconds"] / r["warm"]["seconds"]
+        rec[name] = r
     return rec
 
 

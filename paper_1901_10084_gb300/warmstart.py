@@ -98,3 +98,21 @@ def train(feat: torch.Tensor, target: torch.Tensor, steps=2000, batch=4096, lr=3
     p0 = init_params(seed) if params is None else params
     return _native.cc_mlp_train(p0, feat.data_ptr(), target.data_ptr(), feat.shape[0], batch, steps, lr, seed,
                                 torch.cuda.current_stream(feat.device).cuda_stream)
+
+
+def collect_batch(instances, eps=0.2, tol=1e-4, max_sweeps=20000, tile=16, device=0, group=256):
+    """As ``collect``, solving the instances ``group`` at a time as one
+    batch (one launch per sweep for the whole group); returns
+    (features, targets, sweeps per instance, -1 where not converged)."""
+    from . import Batch
+    feats, targs, sweeps = [], [], []
+    for g0 in range(0, len(instances), group):
+        part = instances[g0:g0 + group]
+        with Batch(part, eps=eps, tile=tile, device=device, check_every=10) as b:
+            _, _, per = b.solve(tol, max_sweeps)
+            for i in range(len(part)):
+                f, t = samples(b.instance(i), device)
+                feats.append(f)
+                targs.append(t)
+            sweeps.extend(per)
+    return torch.cat(feats), torch.cat(targs), sweeps
