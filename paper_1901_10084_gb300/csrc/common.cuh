@@ -71,11 +71,18 @@ __device__ __forceinline__ void st_stream(T* p, T v) { __stcs(p, v); }
 // the correction, projection and dual update of Algorithm 1 collapse to:
 //   z' = max(z + r (x_h - x_a - x_b), 0),  c = z - z',
 //   x_h += c w_h^-1,  x_a -= c w_a^-1,  x_b -= c w_b^-1,  z = z'.
+// v > 0 by an integer test of the sign and magnitude bits (for doubles this
+// keeps the comparison off the FP64 unit): a non-NaN float or double is > 0
+// exactly when its bit pattern, read as a signed integer, is > 0 (-0.0 reads
+// as the most negative integer).
+__device__ __forceinline__ bool positive(double v) { return __double_as_longlong(v) > 0; }
+__device__ __forceinline__ bool positive(float v) { return __float_as_int(v) > 0; }
+
 template <typename T, bool UNITW>
 __device__ __forceinline__ void metric_row_fused(T& xh, T& xa, T& xb, T wh, T wa, T wb, T r, T& z) {
   T d0 = (xh - xa) - xb;
   T zn = fma(d0, r, z);
-  zn = zn > T(0) ? zn : T(0);
+  zn = positive(zn) ? zn : T(0);
   T c = z - zn;
   if (UNITW) {
     xh = xh + c;
@@ -152,14 +159,14 @@ __device__ __forceinline__ void pair_rows(T& x, T& f, T d, T wv, T eps, T& zp, T
     T r = T(1) / (wv + wv);
     T d0 = (x - f) - d;                 // row +: a = (+1, -1), b = d
     T zn = fma(d0, r, zp);
-    zn = zn > T(0) ? zn : T(0);
+    zn = positive(zn) ? zn : T(0);
     T c = zp - zn;
     x = fma(c, wv, x);
     f = fma(-c, wv, f);
     zp = zn;
     d0 = (d - x) - f;                   // row -: a = (-1, -1), b = -d
     zn = fma(d0, r, zm);
-    zn = zn > T(0) ? zn : T(0);
+    zn = positive(zn) ? zn : T(0);
     c = zm - zn;
     x = fma(-c, wv, x);
     f = fma(-c, wv, f);

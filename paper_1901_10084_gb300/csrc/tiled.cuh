@@ -193,19 +193,88 @@ __global__ void __launch_bounds__(TileCfg<B>::NT) k_sweep_tiled(TiledArgs<T> a) 
 // sweep's in value.  Warps whose 32 triplets are all inactive skip the FP64
 // work entirely (a warp vote).
 
+// Float copy of a double for the filters: sign, exponent and the leading 23
+// bits of the significand (truncated), built with integer operations only (a
+// double-to-float conversion instruction would occupy the FP64 unit, which
+// issues one warp instruction per 64 cycles).  |f - x| < 2^-23 |x| for
+// 2^-126 <= |x| < 2^128; below, f = +-0 and |f - x| < 2^-126.
+__device__ __forceinline__ float f32_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);      // biased double exponent
+  if (e < 897) return __uint_as_float(sign);      // below 2^-126
+  if (e > 1150) return __uint_as_float(sign | 0x7f800000u);
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return __uint_as_float(sign | ((unsigned)(e - 896) << 23) | m);
+}
+
 // All three rows of a triplet proved satisfied from float values.  The
 // largest row delta is 2 max(x) - sum(x); evaluated in float from values
-// rounded to nearest (or exact, for FP32 state) it is within 8 * 2^-24 * S =
-// 2^-21 S of the exact one (S = |x_ij| + |x_ik| + |x_jk|; three conversions,
-// two additions and one fused multiply-add, each rounded to nearest), so
-// dmax <= -(2^-20 S + 2^-100) proves every row delta < 0 with a margin far
-// above the rounding of the double (or float) row evaluation itself.
+// within 2^-23 |x| of the doubles (f32_trunc; rounding to nearest is closer)
+// or exact (FP32 state), it is within 11 * 2^-24 * S + 2^-123 of the exact
+// one (S = |x_ij| + |x_ik| + |x_jk|; three conversions, two additions and one
+// fused multiply-add), so dmax <= -(2^-20 S + 2^-100) proves every row delta
+// < 0 with a margin far above the rounding of the double (or float) row
+// evaluation itself.
 __device__ __forceinline__ bool inactive_fast(float a, float b, float c) {
   const float sum = (a + b) + c;
   const float mx = fmaxf(fmaxf(a, b), c);
   const float dmax = fmaf(2.0f, mx, -sum);
   const float S = (fabsf(a) + fabsf(b)) + fabsf(c);
   return dmax <= -fmaf(S, 0x1p-20f, 0x1p-100f);
+}
+
+// Tests on dual values by their bit patterns (integer instructions; an FP64
+// comparison would take 64 issue cycles of the FP64 unit).  Duals are never
+// NaN; nz() treats -0.0 as zero like the value test, differs() compares bit
+// patterns (a +-0 change would count as a change, and only costs a store).
+__device__ __forceinline__ bool nz(double v) { return (__double_as_longlong(v) << 1) != 0; }
+__device__ __forceinline__ bool nz(float v) { return (__float_as_int(v) << 1) != 0; }
+__device__ __forceinline__ bool differs(double a, double b) { return __double_as_longlong(a) != __double_as_longlong(b); }
+__device__ __forceinline__ bool differs(float a, float b) { return __float_as_int(a) != __float_as_int(b); }
+
+__device__ __forceinline__ float to_shadow(double v) { return f32_trunc(v); }
+__device__ __forceinline__ float to_shadow(float v) { return v; }
+
+// One row (x_h against x_a, x_b) proved satisfied from float values: its
+// delta (x_h - x_a) - x_b in float is within 10 * 2^-24 * S + 2^-123 of the
+// exact one (three conversions as above, two additions), so the same test
+// proves delta < 0; with a zero dual the fused row update is then a no-op.
+__device__ __forceinline__ bool row_inactive(float h, float a, float b) {
+  const float d = (h - a) - b;
+  const float S = (fabsf(h) + fabsf(a)) + fabsf(b);
+  return d <= -fmaf(S, 0x1p-20f, 0x1p-100f);
+}
+
+// The three rows of a triplet in FP64 state, skipping each row that is
+// proved a no-op (zero dual, row satisfied in the float test above); the
+// float copies follow every executed row.  Executing a skipped row would
+// give z' = max(r * delta, 0) = 0 and c = 0, so the values equal those of
+// triplet_rows; only the FP64 instructions of the skipped rows are saved
+// (each costs 64 issue cycles of the warp whatever its active lanes).
+template <bool UNITW>
+__device__ __forceinline__ void triplet_rows_skip(double& xij, double& xik, double& xjk, float& fij, float& fik,
+                                                  float& fjk, double vij, double vik, double vjk, double r,
+                                                  double& z0, double& z1, double& z2) {
+  if (nz(z0) || !row_inactive(fij, fik, fjk)) {
+    metric_row_fused<double, UNITW>(xij, xik, xjk, vij, vik, vjk, r, z0);
+    fij = f32_trunc(xij);
+    fik = f32_trunc(xik);
+    fjk = f32_trunc(xjk);
+  }
+  if (nz(z1) || !row_inactive(fik, fij, fjk)) {
+    metric_row_fused<double, UNITW>(xik, xij, xjk, vik, vij, vjk, r, z1);
+    fij = f32_trunc(xij);
+    fik = f32_trunc(xik);
+    fjk = f32_trunc(xjk);
+  }
+  if (nz(z2) || !row_inactive(fjk, fij, fik)) {
+    metric_row_fused<double, UNITW>(xjk, xij, xik, vjk, vij, vik, r, z2);
+    fij = f32_trunc(xij);
+    fik = f32_trunc(xik);
+    fjk = f32_trunc(xjk);
+  }
 }
 
 template <int B>
@@ -377,25 +446,25 @@ __device__ __forceinline__ int flow_subphases(const TiledArgs<T>& a, int w, Flow
           triplet_rows<T, false, UNITW>(xij, xik, xjk, vij, vik, vjk, a.eps, a.r_unit, z0, z1, z2);
           if constexpr (FULL) {
             xr[q] = xij;
-            fr[q] = (float)xij;
+            fr[q] = to_shadow(xij);
           } else {
             pIJ[eij] = xij;
-            if constexpr (SHADOW) gIJ[eij] = (float)xij;
+            if constexpr (SHADOW) gIJ[eij] = to_shadow(xij);
           }
           pIK[eik] = xik;
           pJK[ejk] = xjk;
           if constexpr (SHADOW) {
-            gIK[eik] = (float)xik;
-            gJK[ejk] = (float)xjk;
+            gIK[eik] = to_shadow(xik);
+            gJK[ejk] = to_shadow(xjk);
           }
-          if (z0 != o0) st_stream(zs + slot, z0);
-          if (z1 != o1) st_stream(zs + C::BB + slot, z1);
-          if (z2 != o2) st_stream(zs + 2 * C::BB + slot, z2);
+          if (differs(z0, o0)) st_stream(zs + slot, z0);
+          if (differs(z1, o1)) st_stream(zs + C::BB + slot, z1);
+          if (differs(z2, o2)) st_stream(zs + 2 * C::BB + slot, z2);
           touched = 1;
         }
-        const uint32_t n0 = __ballot_sync(0xffffffffu, need ? (z0 != T(0)) : b0);
-        const uint32_t n1 = __ballot_sync(0xffffffffu, need ? (z1 != T(0)) : b1);
-        const uint32_t n2 = __ballot_sync(0xffffffffu, need ? (z2 != T(0)) : b2);
+        const uint32_t n0 = __ballot_sync(0xffffffffu, need ? nz(z0) : b0);
+        const uint32_t n1 = __ballot_sync(0xffffffffu, need ? nz(z1) : b1);
+        const uint32_t n2 = __ballot_sync(0xffffffffu, need ? nz(z2) : b2);
         if (lane == 0) {
           uint32_t* mw = a.mask + (int64_t)w * M::PER_BT;
           if (n0 != m0) mw[q0] = n0;
@@ -472,7 +541,10 @@ __device__ __forceinline__ int flow_subphases_compact(const TiledArgs<T>& a, Flo
     item_sync<WARP>();
     const int cnt = sm.lcnt[t];
     if (cnt > 0) {
-      for (int p = tid; p < cnt; p += NTH) {
+      // list entry p goes to warp p % NW: a few updates land on different
+      // warps (different SM sub-partitions, each with its own FP64 issue)
+      constexpr int NWL = NTH / 32;
+      for (int p = (tid & 31) * NWL + (tid >> 5); p < cnt; p += NTH) {
         const int slot = sm.lslot[p];
         const int la = slot / B, lb = slot % B, lc = (t - la - lb) & (B - 1);
         const int eij = slot, eik = la * B + lc, ejk = lb * B + lc;
@@ -485,35 +557,39 @@ __device__ __forceinline__ int flow_subphases_compact(const TiledArgs<T>& a, Flo
           vik = a.winv[oIK + eik];
           vjk = a.winv[oJK + ejk];
         }
-        triplet_rows<T, false, UNITW>(xij, xik, xjk, vij, vik, vjk, a.eps, a.r_unit, z0, z1, z2);
+        if constexpr (SHADOW) {
+          float fij = gIJ[eij], fik = gIK[eik], fjk = gJK[ejk];
+          const T r = UNITW ? a.r_unit : T(1) / ((vij + vik) + vjk);
+          triplet_rows_skip<UNITW>(xij, xik, xjk, fij, fik, fjk, vij, vik, vjk, r, z0, z1, z2);
+          gIJ[eij] = fij;
+          gIK[eik] = fik;
+          gJK[ejk] = fjk;
+        } else {
+          triplet_rows<T, false, UNITW>(xij, xik, xjk, vij, vik, vjk, a.eps, a.r_unit, z0, z1, z2);
+        }
         pIJ[eij] = xij;
         pIK[eik] = xik;
         pJK[ejk] = xjk;
-        if constexpr (SHADOW) {
-          gIJ[eij] = (float)xij;
-          gIK[eik] = (float)xik;
-          gJK[ejk] = (float)xjk;
-        }
         const uint32_t bit = 1u << (slot & 31);
         const int wq = qt + (slot >> 5);
-        if (z0 != o0) {
+        if (differs(z0, o0)) {
           st_stream(zs + slot, z0);
-          if ((z0 != T(0)) != (o0 != T(0))) {
-            if (z0 != T(0)) atomicOr(&sm.mask[wq], bit); else atomicAnd(&sm.mask[wq], ~bit);
+          if (nz(z0) != nz(o0)) {
+            if (nz(z0)) atomicOr(&sm.mask[wq], bit); else atomicAnd(&sm.mask[wq], ~bit);
             sm.dirty = 1;
           }
         }
-        if (z1 != o1) {
+        if (differs(z1, o1)) {
           st_stream(zs + C::BB + slot, z1);
-          if ((z1 != T(0)) != (o1 != T(0))) {
-            if (z1 != T(0)) atomicOr(&sm.mask[wq + M::WPR], bit); else atomicAnd(&sm.mask[wq + M::WPR], ~bit);
+          if (nz(z1) != nz(o1)) {
+            if (nz(z1)) atomicOr(&sm.mask[wq + M::WPR], bit); else atomicAnd(&sm.mask[wq + M::WPR], ~bit);
             sm.dirty = 1;
           }
         }
-        if (z2 != o2) {
+        if (differs(z2, o2)) {
           st_stream(zs + 2 * C::BB + slot, z2);
-          if ((z2 != T(0)) != (o2 != T(0))) {
-            if (z2 != T(0)) atomicOr(&sm.mask[wq + 2 * M::WPR], bit); else atomicAnd(&sm.mask[wq + 2 * M::WPR], ~bit);
+          if (nz(z2) != nz(o2)) {
+            if (nz(z2)) atomicOr(&sm.mask[wq + 2 * M::WPR], bit); else atomicAnd(&sm.mask[wq + 2 * M::WPR], ~bit);
             sm.dirty = 1;
           }
         }
@@ -630,9 +706,9 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
   }
   if constexpr (SHADOW) {
     for (int e = tid; e < C::BB; e += NTH) {
-      sm.f[0][e] = (float)sm.x[0][e];
-      if (!kj) sm.f[SHADOW ? 1 : 0][e] = (float)sm.x[1][e];
-      if (!ij) sm.f[SHADOW ? 2 : 0][e] = (float)sm.x[2][e];
+      sm.f[0][e] = f32_trunc(sm.x[0][e]);
+      if (!kj) sm.f[SHADOW ? 1 : 0][e] = f32_trunc(sm.x[1][e]);
+      if (!ij) sm.f[SHADOW ? 2 : 0][e] = f32_trunc(sm.x[2][e]);
     }
   }
   cp_async_wait_all();

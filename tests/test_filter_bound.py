@@ -65,3 +65,70 @@ def test_filter_is_sound_for_fp32_state():
         d1 = (f[:, 1] - f[:, 0]) - f[:, 2]
         d2 = (f[:, 2] - f[:, 0]) - f[:, 1]
         assert np.all(np.maximum(np.maximum(d0, d1), d2)[ok] < 0)
+
+
+def f32_trunc(x):
+    """The kernels' integer double-to-float copy: sign, exponent and the
+    leading 23 significand bits; +-0 below 2^-126."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    b = x.view(np.uint64)
+    hi = (b >> np.uint64(32)).astype(np.uint32)
+    lo = (b & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    sign = hi & np.uint32(0x80000000)
+    e = ((hi >> np.uint32(20)) & np.uint32(0x7FF)).astype(np.int64)
+    m = ((hi & np.uint32(0xFFFFF)) << np.uint32(3)) | (lo >> np.uint32(29))
+    body = (np.clip(e - 896, 0, 255).astype(np.uint32) << np.uint32(23)) | m
+    out = np.where(e < 897, sign, sign | body)
+    out = np.where(e > 1150, sign | np.uint32(0x7F800000), out)
+    return out.astype(np.uint32).view(np.float32)
+
+
+def row_inactive(h, a, b):
+    d = (h - a) - b
+    S = (np.abs(h) + np.abs(a)) + np.abs(b)
+    return d <= -_fma32(S, TAU_REL * np.ones_like(S), TAU_ABS * np.ones_like(S))
+
+
+def test_truncated_copy_error_bound():
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-2, 2, 400000) * rng.choice([1e-30, 1e-6, 1.0, 1e3, 1e30], 400000)
+    f = f32_trunc(x).astype(np.float64)
+    assert np.all(np.abs(f - x) < 2.0 ** -23 * np.abs(x))
+    assert np.all(np.abs(f) <= np.abs(x)) and np.all(np.sign(f) == np.sign(x))
+    tiny = np.array([1e-40, -1e-45, 2.0 ** -127, 0.0, -0.0])
+    assert np.all(f32_trunc(tiny) == 0.0)
+    exact = np.array([1.0, -0.75, 2.0 ** -126, 3.0 * 2.0 ** 100])     # 23-bit significands stay exact
+    assert np.array_equal(f32_trunc(exact).astype(np.float64), exact)
+
+
+def test_filter_is_sound_with_truncated_copies():
+    rng = np.random.default_rng(6)
+    for _ in range(20):
+        x = _cases(rng, 200000)
+        f = f32_trunc(x.ravel()).reshape(x.shape)
+        ok = inactive_fast(f[:, 0], f[:, 1], f[:, 2])
+        d0 = (x[:, 0] - x[:, 1]) - x[:, 2]
+        d1 = (x[:, 1] - x[:, 0]) - x[:, 2]
+        d2 = (x[:, 2] - x[:, 0]) - x[:, 1]
+        assert np.all(np.maximum(np.maximum(d0, d1), d2)[ok] < 0)
+        assert ok.mean() > 0.05
+
+
+def test_row_filter_is_sound_and_the_skipped_row_is_a_no_op():
+    """row_inactive on float copies (truncated or rounded) proves the double
+    row delta negative; with a zero dual the fused row update then leaves
+    z' = max(fma(delta, 1/3, 0), 0) = 0 and c = 0."""
+    rng = np.random.default_rng(7)
+    for copy in (f32_trunc, lambda v: v.astype(np.float32)):
+        hits = 0
+        for _ in range(10):
+            x = _cases(rng, 200000)
+            f = copy(x.ravel()).reshape(x.shape)
+            for h, a, b in ((0, 1, 2), (1, 0, 2), (2, 0, 1)):
+                ok = row_inactive(f[:, h], f[:, a], f[:, b])
+                d = (x[:, h] - x[:, a]) - x[:, b]
+                assert np.all(d[ok] < 0)
+                zn = d[ok] * (1.0 / 3.0)        # fma(d, r, 0) = round(d * r): same sign as d
+                assert np.all(np.maximum(zn, 0.0) == 0.0)
+                hits += ok.sum()
+        assert hits > 0
