@@ -88,10 +88,14 @@ typedef struct cc_opts {
   int32_t debug_skip_cta;   /* test hook: this CTA skips its first barrier
                                arrival (-1 = off); the sweep then ends with
                                CC_ERR_TIMEOUT */
-  int32_t variant;          /* fused-form sweep kernel: 0 or 1 = one CTA per
-                               block triple (default), 2 = one warp per block
-                               triple (tile <= 16), 3 = one half-size CTA per
-                               block triple (tile >= 16) */
+  int32_t variant;          /* fused-form sweep kernel: 0 = one CTA per block
+                               triple (default); 1 = the same with compacted
+                               update lists in FP64 state; 2 = one warp per
+                               block triple (tile <= 16); 3 = one half-size
+                               CTA per block triple (tile >= 16); 4 = as 0
+                               with the float filters off (every triplet and
+                               row updated: the reference the filtered forms
+                               equal in value).  All give the same values. */
   double refine_at;         /* CC_PREC_FP32_REFINE: cc_solve leaves FP32 when
                                the violation is <= max(tol, refine_at) or stops
                                decreasing between checks; default 1e-5 */
@@ -186,7 +190,9 @@ int cc_set_duals(cc_handle* h, const double* y_tri, const double* y_pair);
 /* Per-work-item timestamps of the most recent fused tiled sweep (opts.trace
  * = 1): 6 uint64 per item in schedule order (block triples, then one pair
  * item per tile): taken, dependencies met, processed, released (ns, GPU
- * global timer; 0 where not applicable), unused, CTA index.  Copies
+ * global timer; 0 where not applicable), counts (bits 0-23: nonzero
+ * triangle duals staged; FP64 state only: 24-39 triplets updated, 40-55
+ * rows executed, 56-63 sub-phases with updates), CTA index.  Copies
  * min(cap, items) records into out (host); returns the number copied, the
  * item count when out is NULL, 0 when tracing is off, -1 on a CUDA error.
  * Synchronizes. */

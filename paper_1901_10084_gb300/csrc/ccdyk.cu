@@ -235,6 +235,8 @@ TiledArgs<T> tiled_args(cc_handle* h) {
   a.work = nullptr;
   a.nbt = h->nbt;
   a.trace = h->trace;
+  a.compact = h->o.variant == 1 ? 1 : 0;
+  a.nofilter = h->o.variant == 4 ? 1 : 0;
   return a;
 }
 
@@ -587,6 +589,7 @@ int check_opts(const cc_opts& o) {
   if (o.precision == CC_PREC_FP32_REFINE && o.schedule != CC_SCHED_TILED)
     return fail(nullptr, CC_ERR_ARG, "the FP32 bulk form runs on the tiled schedule");
   if (o.check_every < 1) return fail(nullptr, CC_ERR_ARG, "check_every must be >= 1");
+  if (o.variant < 0 || o.variant > 4) return fail(nullptr, CC_ERR_ARG, "variant must be 0..4");
   if (!(o.barrier_timeout_s > 0.0)) return fail(nullptr, CC_ERR_ARG, "barrier_timeout_s must be > 0");
   if ((o.alloc == nullptr) != (o.free == nullptr)) return fail(nullptr, CC_ERR_ARG, "alloc and free go together");
   return CC_OK;

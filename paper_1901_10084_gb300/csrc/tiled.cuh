@@ -52,6 +52,8 @@ struct TiledArgs {
   int nbt;              // block triples per sweep
   unsigned long long* trace;  // optional per-item timestamps (nullptr = off)
   int* cnt;             // per-tile visit counters of this instance (batched sweep)
+  int compact;          // FP64 CTA items: 1 = compacted update lists per sub-phase
+  int nofilter;         // 1: update every triplet and row (reference for the filters)
 };
 
 __device__ __forceinline__ void unpack_bt(int pk, int& I, int& J, int& K) {
@@ -254,27 +256,32 @@ __device__ __forceinline__ bool row_inactive(float h, float a, float b) {
 // triplet_rows; only the FP64 instructions of the skipped rows are saved
 // (each costs 64 issue cycles of the warp whatever its active lanes).
 template <bool UNITW>
-__device__ __forceinline__ void triplet_rows_skip(double& xij, double& xik, double& xjk, float& fij, float& fik,
+__device__ __forceinline__ int triplet_rows_skip(double& xij, double& xik, double& xjk, float& fij, float& fik,
                                                   float& fjk, double vij, double vik, double vjk, double r,
-                                                  double& z0, double& z1, double& z2) {
-  if (nz(z0) || !row_inactive(fij, fik, fjk)) {
+                                                  double& z0, double& z1, double& z2, bool all = false) {
+  int rows = 0;
+  if (all || nz(z0) || !row_inactive(fij, fik, fjk)) {
+    ++rows;
     metric_row_fused<double, UNITW>(xij, xik, xjk, vij, vik, vjk, r, z0);
     fij = f32_trunc(xij);
     fik = f32_trunc(xik);
     fjk = f32_trunc(xjk);
   }
-  if (nz(z1) || !row_inactive(fik, fij, fjk)) {
+  if (all || nz(z1) || !row_inactive(fik, fij, fjk)) {
+    ++rows;
     metric_row_fused<double, UNITW>(xik, xij, xjk, vik, vij, vjk, r, z1);
     fij = f32_trunc(xij);
     fik = f32_trunc(xik);
     fjk = f32_trunc(xjk);
   }
-  if (nz(z2) || !row_inactive(fjk, fij, fik)) {
+  if (all || nz(z2) || !row_inactive(fjk, fij, fik)) {
+    ++rows;
     metric_row_fused<double, UNITW>(xjk, xij, xik, vjk, vij, vik, r, z2);
     fij = f32_trunc(xij);
     fik = f32_trunc(xik);
     fjk = f32_trunc(xjk);
   }
+  return rows;
 }
 
 template <int B>
@@ -317,6 +324,8 @@ struct alignas(16) FlowSmem {
   int lcnt[B];              // list length per sub-phase
   int scan[32];
   int item, flag, total, dirty;
+  int ntrip, nrows, nsub;   // trace counters: triplets updated, rows executed, sub-phases with updates
+  unsigned subbits;         //   sub-phases with updates (per-warp form)
 };
 
 __device__ __forceinline__ int ld_relaxed_i32(const int* p) {
@@ -420,9 +429,10 @@ __device__ __forceinline__ int flow_subphases(const TiledArgs<T>& a, int w, Flow
       bool need = false;
       if (valid) {
         const float fij = FULL ? fr[q] : gIJ[eij];
-        need = (b0 | b1 | b2) || !inactive_fast(fij, gIK[eik], gJK[ejk]);
+        need = a.nofilter || (b0 | b1 | b2) || !inactive_fast(fij, gIK[eik], gJK[ejk]);
       }
       if (__any_sync(0xffffffffu, need)) {
+        if (a.trace && lane == 0) atomicOr(&sm.subbits, 1u << t);
         T z0 = T(0), z1 = T(0), z2 = T(0);
         if (need) {
           if (staged) {
@@ -443,20 +453,27 @@ __device__ __forceinline__ int flow_subphases(const TiledArgs<T>& a, int w, Flow
             vik = a.winv[oIK + eik];
             vjk = a.winv[oJK + ejk];
           }
-          triplet_rows<T, false, UNITW>(xij, xik, xjk, vij, vik, vjk, a.eps, a.r_unit, z0, z1, z2);
-          if constexpr (FULL) {
-            xr[q] = xij;
-            fr[q] = to_shadow(xij);
+          if constexpr (SHADOW) {
+            float fij = FULL ? fr[q] : gIJ[eij], fik = gIK[eik], fjk = gJK[ejk];
+            const T r = UNITW ? a.r_unit : T(1) / ((vij + vik) + vjk);
+            const int rows = triplet_rows_skip<UNITW>(xij, xik, xjk, fij, fik, fjk, vij, vik, vjk, r, z0, z1, z2,
+                                                     a.nofilter != 0);
+            if (a.trace) {
+              atomicAdd(&sm.ntrip, 1);
+              atomicAdd(&sm.nrows, rows);
+            }
+            if constexpr (FULL) fr[q] = fij;
+            else gIJ[eij] = fij;
+            gIK[eik] = fik;
+            gJK[ejk] = fjk;
           } else {
-            pIJ[eij] = xij;
-            if constexpr (SHADOW) gIJ[eij] = to_shadow(xij);
+            triplet_rows<T, false, UNITW>(xij, xik, xjk, vij, vik, vjk, a.eps, a.r_unit, z0, z1, z2);
+            if constexpr (FULL) fr[q] = xij;   // FP32 state: the filter reads x_ij itself
           }
+          if constexpr (FULL) xr[q] = xij;
+          else pIJ[eij] = xij;
           pIK[eik] = xik;
           pJK[ejk] = xjk;
-          if constexpr (SHADOW) {
-            gIK[eik] = to_shadow(xik);
-            gJK[ejk] = to_shadow(xjk);
-          }
           if (differs(z0, o0)) st_stream(zs + slot, z0);
           if (differs(z1, o1)) st_stream(zs + C::BB + slot, z1);
           if (differs(z2, o2)) st_stream(zs + 2 * C::BB + slot, z2);
@@ -520,7 +537,7 @@ __device__ __forceinline__ int flow_subphases_compact(const TiledArgs<T>& a, Flo
         m2 = sm.mask[q2];
       }
       const bool b0 = (m0 >> lane) & 1u, b1 = (m1 >> lane) & 1u, b2 = (m2 >> lane) & 1u;
-      if (valid && ((b0 | b1 | b2) || !inactive_fast(gIJ[slot], gIK[la * B + lc], gJK[lb * B + lc]))) {
+      if (valid && (a.nofilter || (b0 | b1 | b2) || !inactive_fast(gIJ[slot], gIK[la * B + lc], gJK[lb * B + lc]))) {
         T z0 = T(0), z1 = T(0), z2 = T(0);
         if (staged) {
           if (b0) z0 = sm.dual[sm.pre[q0] + __popc(m0 & below)];
@@ -544,6 +561,7 @@ __device__ __forceinline__ int flow_subphases_compact(const TiledArgs<T>& a, Flo
       // list entry p goes to warp p % NW: a few updates land on different
       // warps (different SM sub-partitions, each with its own FP64 issue)
       constexpr int NWL = NTH / 32;
+      if (a.trace && tid == 0) ++sm.nsub;
       for (int p = (tid & 31) * NWL + (tid >> 5); p < cnt; p += NTH) {
         const int slot = sm.lslot[p];
         const int la = slot / B, lb = slot % B, lc = (t - la - lb) & (B - 1);
@@ -560,7 +578,12 @@ __device__ __forceinline__ int flow_subphases_compact(const TiledArgs<T>& a, Flo
         if constexpr (SHADOW) {
           float fij = gIJ[eij], fik = gIK[eik], fjk = gJK[ejk];
           const T r = UNITW ? a.r_unit : T(1) / ((vij + vik) + vjk);
-          triplet_rows_skip<UNITW>(xij, xik, xjk, fij, fik, fjk, vij, vik, vjk, r, z0, z1, z2);
+          const int rows = triplet_rows_skip<UNITW>(xij, xik, xjk, fij, fik, fjk, vij, vik, vjk, r, z0, z1, z2,
+                                                     a.nofilter != 0);
+          if (a.trace) {
+            atomicAdd(&sm.ntrip, 1);
+            atomicAdd(&sm.nrows, rows);
+          }
           gIJ[eij] = fij;
           gIK[eik] = fik;
           gJK[ejk] = fjk;
@@ -651,7 +674,13 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
   for (int e = tid; e < MCH; e += NTH)
     cp_async16(reinterpret_cast<char*>(sm.mask) + 16 * e, reinterpret_cast<const char*>(mb) + 16 * e);
   for (int e = tid; e < B; e += NTH) sm.lcnt[e] = 0;
-  if (tid == 0) sm.dirty = 0;
+  if (tid == 0) {
+    sm.dirty = 0;
+    sm.ntrip = 0;
+    sm.nrows = 0;
+    sm.nsub = 0;
+    sm.subbits = 0u;
+  }
   cp_async_wait_all();
   item_sync<WARP>();
 
@@ -716,10 +745,10 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
 
   const int kB = K * B;
   const bool full = (I < J) && (J < K) && (kB + B <= a.n);
-  int touched;
-  // compaction pays for FP64 updates (few warps on the slow FP64 pipe); the
-  // FP32 update is cheap enough that the plain per-warp path is faster
-  if constexpr (WARP || !SHADOW) {
+  int touched = 0;
+  // per-warp form (filter and update in the same thread, one barrier per
+  // sub-phase); compact = 1 selects compacted update lists for FP64 state
+  if (WARP || !SHADOW || a.compact == 0) {
     if (full && total == 0)
       touched = flow_subphases<T, UNITW, B, NTH_, true, false>(a, w, sm, pIJ, pIK, pJK, gIJ, gIK, gJK, oIJ, oIK,
                                                                oJK, false, false, kB, staged, tid, lane, zb);
@@ -730,17 +759,20 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
       touched = flow_subphases<T, UNITW, B, NTH_, false, true>(a, w, sm, pIJ, pIK, pJK, gIJ, gIK, gJK, oIJ, oIK,
                                                                oJK, ij, kj, kB, staged, tid, lane, zb);
   } else {
-    if (full && total == 0)
-      touched = flow_subphases_compact<T, UNITW, B, NTH_, true, false>(a, sm, pIJ, pIK, pJK, gIJ, gIK, gJK, oIJ,
-                                                                       oIK, oJK, false, false, kB, staged, tid,
-                                                                       lane, zb);
-    else if (full)
-      touched = flow_subphases_compact<T, UNITW, B, NTH_, true, true>(a, sm, pIJ, pIK, pJK, gIJ, gIK, gJK, oIJ, oIK,
-                                                                      oJK, false, false, kB, staged, tid, lane, zb);
-    else
-      touched = flow_subphases_compact<T, UNITW, B, NTH_, false, true>(a, sm, pIJ, pIK, pJK, gIJ, gIK, gJK, oIJ,
-                                                                       oIK, oJK, ij, kj, kB, staged, tid, lane,
-                                                                       zb);
+    if constexpr (SHADOW && !WARP) {
+      if (full && total == 0)
+        touched = flow_subphases_compact<T, UNITW, B, NTH_, true, false>(a, sm, pIJ, pIK, pJK, gIJ, gIK, gJK, oIJ,
+                                                                         oIK, oJK, false, false, kB, staged, tid,
+                                                                         lane, zb);
+      else if (full)
+        touched = flow_subphases_compact<T, UNITW, B, NTH_, true, true>(a, sm, pIJ, pIK, pJK, gIJ, gIK, gJK, oIJ,
+                                                                        oIK, oJK, false, false, kB, staged, tid,
+                                                                        lane, zb);
+      else
+        touched = flow_subphases_compact<T, UNITW, B, NTH_, false, true>(a, sm, pIJ, pIK, pJK, gIJ, gIK, gJK, oIJ,
+                                                                         oIK, oJK, ij, kj, kB, staged, tid, lane,
+                                                                         zb);
+    }
   }
   bool any_touched;
   if constexpr (WARP) any_touched = __any_sync(0xffffffffu, touched);
@@ -823,7 +855,8 @@ __global__ void __launch_bounds__(NT) k_sweep_flow(TiledArgs<T> a, int* flow) {
       flow_block_triple<T, UNITW, B, NT>(a, w, I, J, K, sm);
       if (tr && threadIdx.x == 0) {
         tr[2] = global_ns();
-        tr[4] = (unsigned long long)sm.total;
+        tr[4] = (unsigned long long)min(sm.total, 0xffffff) | ((unsigned long long)min(sm.ntrip, 0xffff) << 24) |
+                ((unsigned long long)min(sm.nrows, 0xffff) << 40) | ((unsigned long long)min(sm.nsub + __popc(sm.subbits), 0xff) << 56);
       }
       if (first && (int)blockIdx.x == a.skip_cta) return;   // fault injection: never release
       if (threadIdx.x == 0) release_tiles(tile_cnt, tIJ, u1, u2);

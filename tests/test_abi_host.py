@@ -41,7 +41,8 @@ def test_opts_defaults(lib):
 
 @pytest.mark.parametrize("field,value", [("eps", 0.0), ("eps", -1.0), ("eps", float("inf")),
                                          ("tile", 12), ("check_every", 0),
-                                         ("barrier_timeout_s", 0.0), ("precision", 7)])
+                                         ("barrier_timeout_s", 0.0), ("precision", 7), ("variant", 5),
+                                         ("variant", -1)])
 def test_bad_options_rejected_before_device_work(lib, field, value):
     import numpy as np
     from paper_1901_10084_gb300 import _native as N

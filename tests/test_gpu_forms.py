@@ -1,0 +1,77 @@
+"""The FP64 sweep's per-warp form (default) and compacted form (variant 1)
+update the same triplets with the same arithmetic, so their iterates, duals
+and nonzero-dual masks agree bit for bit; and a sweep is deterministic (the
+dataflow order inside a sub-phase never changes a result).  GPU."""
+import numpy as np
+import pytest
+
+from instances import chung_lu, planted_partition
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(n, d, w, sweeps, solve=None, **kw):
+    import paper_1901_10084_gb300 as cc
+    with cc.Solver(n, d, w, **kw) as s:
+        if solve is None:
+            s.sweep(sweeps)
+        else:
+            s.solve(solve, sweeps)
+        x, f = s.get_x()
+        yt, yp = s.get_duals()
+        st = s.stats()
+    return x, f, yt, yp, st
+
+
+CASES = [(60, 8, False, False), (61, 16, False, True), (130, 16, True, False), (200, 16, False, True),
+         (97, 32, True, True), (300, 32, False, False)]
+
+
+@pytest.mark.parametrize("n,tile,weighted,interleave", CASES)
+def test_per_warp_and_compacted_fp64_forms_agree_bitwise(n, tile, weighted, interleave):
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=n + tile, weights=(0.5, 2.0) if weighted else None)
+    kw = dict(tile=tile, interleave=interleave)
+    a = _run(n, d, w, 25, variant=0, **kw)
+    b = _run(n, d, w, 25, variant=1, **kw)
+    for u, v in zip(a[:4], b[:4]):
+        assert np.array_equal(u, v)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("n,tile,weighted,interleave", CASES[1:4])
+def test_sweeps_are_deterministic(n, tile, weighted, interleave, precision):
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=n + 1, weights=(0.5, 2.0) if weighted else None)
+    kw = dict(tile=tile, interleave=interleave, precision=precision)
+    a = _run(n, d, w, 30, **kw)
+    b = _run(n, d, w, 30, **kw)
+    for u, v in zip(a[:4], b[:4]):
+        assert np.array_equal(u, v)
+
+
+def test_fp32_refine_solve_is_deterministic_and_forms_agree():
+    n = 250
+    d, w, _ = planted_partition(n, 5, 0.6, 0.1, seed=8)
+    runs = [_run(n, d, w, 2000, solve=1e-6, tile=16, precision="fp32_refine", variant=v) for v in (0, 0, 1)]
+    for r in runs[1:]:
+        for u, v in zip(runs[0][:4], r[:4]):
+            assert np.array_equal(u, v)
+        assert r[4]["sweeps"] == runs[0][4]["sweeps"] and r[4]["fp32_sweeps"] == runs[0][4]["fp32_sweeps"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("n,tile,weighted,interleave", CASES)
+def test_filtered_forms_equal_the_unfiltered_sweep(n, tile, weighted, interleave, precision):
+    """Variant 4 updates every triplet and every row; the float filters only
+    skip updates that are no-ops, so the filtered sweeps give the same values
+    (x + 0 may turn -0.0 into +0.0, which compares equal)."""
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=3 * n + tile, weights=(0.5, 2.0) if weighted else None)
+    kw = dict(tile=tile, interleave=interleave, precision=precision)
+    ref = _run(n, d, w, 20, variant=4, **kw)
+    for v in (0, 1, 3):
+        got = _run(n, d, w, 20, variant=v, **kw)
+        for u, r in zip(got[:4], ref[:4]):
+            assert np.array_equal(u, r), v
+    if tile <= 16:
+        got = _run(n, d, w, 20, variant=2, **kw)
+        for u, r in zip(got[:4], ref[:4]):
+            assert np.array_equal(u, r)
