@@ -80,6 +80,12 @@ def _load():
         lib.ora_max_violation.restype = dbl
         lib.ora_objectives.argtypes = [i64, dbl, dp, dp, dp, dp, dp, dp]
         lib.ora_objectives.restype = None
+        lib.ora_init_l2.argtypes = [i64, dp, dp, dp, dp, dp]
+        lib.ora_init_l2.restype = None
+        lib.ora_sweep_l2.argtypes = [i64, i32, i64, dp, dp, dp, i64]
+        lib.ora_sweep_l2.restype = i64
+        lib.ora_objectives_l2.argtypes = [i64, dp, dp, dp, dp]
+        lib.ora_objectives_l2.restype = None
         _lib = lib
         return lib
 
@@ -106,11 +112,18 @@ def trank(n: int, i: int, j: int, k: int) -> int:
 
 
 class State:
-    """Oracle state: x, f (packed pairs), y_tri (canonical), y_pair."""
+    """Oracle state: x, f (packed pairs), y_tri (canonical), y_pair.
 
-    def __init__(self, n: int, d: np.ndarray, w: np.ndarray, eps: float):
+    problem "cc": the regularized CC LP (Eq. mn1 as Eq. qp, parameter eps);
+    problem "l2": l2 metric nearness, min sum w (x - d)^2 over the metric rows
+    (Eq. metricnear, p = 2; Eq. qp with eps = 1, c = -W d; f and y_pair stay 0)."""
+
+    def __init__(self, n: int, d: np.ndarray, w: np.ndarray, eps: float = 1.0, problem: str = "cc"):
+        if problem not in ("cc", "l2"):
+            raise ValueError(problem)
+        self.problem = problem
         self.n = int(n)
-        self.eps = float(eps)
+        self.eps = float(eps) if problem == "cc" else 1.0
         P, T = num_pairs(n), num_triplets(n)
         self.d = np.ascontiguousarray(d, dtype=np.float64)
         self.w = np.ascontiguousarray(w, dtype=np.float64)
@@ -120,12 +133,18 @@ class State:
         self.f = np.empty(P)
         self.ytri = np.empty(3 * T)
         self.ypair = np.empty(2 * P)
-        _load().ora_init(n, self.eps, _dp(self.w), _dp(self.winv), _dp(self.x),
-                         _dp(self.f), _dp(self.ytri), _dp(self.ypair))
+        if problem == "cc":
+            _load().ora_init(n, self.eps, _dp(self.w), _dp(self.winv), _dp(self.x),
+                             _dp(self.f), _dp(self.ytri), _dp(self.ypair))
+        else:
+            _load().ora_init_l2(n, _dp(self.d), _dp(self.w), _dp(self.winv), _dp(self.x),
+                                _dp(self.ytri))
+            self.f[:] = 0.0
+            self.ypair[:] = 0.0
 
     def copy(self) -> "State":
         s = State.__new__(State)
-        s.n, s.eps = self.n, self.eps
+        s.n, s.eps, s.problem = self.n, self.eps, self.problem
         for k in ("d", "w", "winv", "x", "f", "ytri", "ypair"):
             setattr(s, k, getattr(self, k).copy())
         return s
@@ -133,6 +152,9 @@ class State:
     def sweep(self, schedule: int = 1, tile: int = 16, max_rows: int = -1) -> int:
         """One pass over all rows in the schedule's order (or its first
         ``max_rows`` rows).  Returns the number of rows visited."""
+        if self.problem == "l2":
+            return int(_load().ora_sweep_l2(self.n, schedule, tile, _dp(self.winv), _dp(self.x),
+                                            _dp(self.ytri), max_rows))
         return int(_load().ora_sweep(self.n, schedule, tile, self.eps, _dp(self.d),
                                      _dp(self.winv), _dp(self.x), _dp(self.f),
                                      _dp(self.ytri), _dp(self.ypair), max_rows))
@@ -149,9 +171,14 @@ class State:
         return float(_load().ora_max_violation(self.n, _dp(self.x)))
 
     def objectives(self) -> dict:
+        """cc: lp = sum w |x - d|; l2: lp = sum w (x - d)^2 (the problem's
+        objective), qp_primal / dual / gap of the respective Eq. qp."""
         out = np.zeros(5)
-        _load().ora_objectives(self.n, self.eps, _dp(self.d), _dp(self.w), _dp(self.x),
-                               _dp(self.f), _dp(self.ypair), _dp(out))
+        if self.problem == "l2":
+            _load().ora_objectives_l2(self.n, _dp(self.d), _dp(self.w), _dp(self.x), _dp(out))
+        else:
+            _load().ora_objectives(self.n, self.eps, _dp(self.d), _dp(self.w), _dp(self.x),
+                                   _dp(self.f), _dp(self.ypair), _dp(out))
         return {"lp": out[0], "qp_primal": out[1], "dual": out[2],
                 "pair_violation": out[3], "wf": out[4], "gap": out[1] - out[2]}
 

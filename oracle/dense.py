@@ -107,3 +107,50 @@ def dual_objective(n, d, w, eps, ytri, ypair) -> float:
     winv = np.concatenate([1.0 / w, 1.0 / w])
     g = c + A.T @ y
     return float(-b @ y - 0.5 / eps * np.sum(winv * g * g))
+
+
+# ---- l2 metric nearness (Eq. metricnear, p = 2) -------------------------------
+
+def metric_matrix(n: int):
+    """Sparse A (3T x P) of the metric rows alone, rows in the order of
+    ``constraint_matrix`` (hypotenuse ij, ik, jk per triplet)."""
+    pm = pair_map(n)
+    rows, cols, vals = [], [], []
+    r = 0
+    for (i, j, k) in itertools.combinations(range(n), 3):
+        ij, ik, jk = pm[(i, j)], pm[(i, k)], pm[(j, k)]
+        for h, a1, a2 in ((ij, ik, jk), (ik, ij, jk), (jk, ij, ik)):
+            rows += [r, r, r]
+            cols += [h, a1, a2]
+            vals += [1.0, -1.0, -1.0]
+            r += 1
+    return sp.csr_matrix((vals, (rows, cols)), shape=(r, len(pm)))
+
+
+def l2_optimum(n: int, d: np.ndarray, w: np.ndarray):
+    """min sum w (x - d)^2 s.t. the metric rows, through its dual: with
+    M = W^{-1/2} A^T and q = W^{1/2} d the dual is min_{y >= 0} ||M y - q||,
+    a non-negative least-squares problem (scipy's active-set NNLS); the
+    unique primal solution is x = d - W^{-1} A^T y.  Returns (x, y)."""
+    from scipy.optimize import nnls
+    A = metric_matrix(n).toarray()
+    M = (A / np.sqrt(w)[None, :]).T
+    y, _ = nnls(M, np.sqrt(w) * d, maxiter=50 * A.shape[0])
+    x = d - (A.T @ y) / w
+    return x, y
+
+
+def l2_kkt(n: int, d: np.ndarray, w: np.ndarray, x: np.ndarray, ytri: np.ndarray) -> dict:
+    """KKT residuals of min (1/2) sum w (x - d)^2 s.t. A x <= 0 at (x, y)."""
+    A = metric_matrix(n)
+    ax = A @ x
+    return {"primal": float(max(0.0, ax.max())), "dual_neg": float(max(0.0, -ytri.min())),
+            "compl": float(np.max(np.abs(ytri * ax))),
+            "stationarity": float(np.max(np.abs(w * (x - d) + A.T @ ytri)))}
+
+
+def l2_dual_objective(n: int, d: np.ndarray, w: np.ndarray, ytri: np.ndarray) -> float:
+    """y^T A d - (1/2) y^T A W^{-1} A^T y, evaluated from y directly."""
+    A = metric_matrix(n)
+    aty = A.T @ ytri
+    return float(ytri @ (A @ d) - 0.5 * np.sum(aty * aty / w))

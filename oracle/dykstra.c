@@ -332,3 +332,52 @@ void ora_objectives(int64_t n, double eps, const double* d, const double* w,
   out[3] = pv;
   out[4] = wf;
 }
+
+/* ---- l2 metric nearness (Sec. II-A, Eq. metricnear with p = 2) -----------
+ * min sum_{i<j} w_ij (x_ij - d_ij)^2 subject to the metric rows only (for
+ * n >= 3 they imply x >= 0).  As an instance of Eq. qp: v = x, W = diag(w),
+ * eps = 1, c = -W d, b = 0, so Algorithm 1 starts from
+ * x = -(1/eps) W^{-1} c = d with y = 0 and visits only metric rows; its dual
+ * y is the multiplier of (1/2) sum w (x - d)^2. */
+
+/* Algorithm 1's initialisation for this instance of Eq. qp. */
+void ora_init_l2(int64_t n, const double* d, const double* w, double* winv, double* x,
+                 double* ytri) {
+  int64_t P = ch2(n), T = ch3(n);
+  for (int64_t p = 0; p < P; ++p) {
+    winv[p] = 1.0 / w[p];
+    x[p] = d[p];                          /* -(1/eps) W^{-1} c = W^{-1} W d = d */
+  }
+  for (int64_t t = 0; t < 3 * T; ++t) ytri[t] = 0.0;
+}
+
+/* One sweep over the metric rows only (every triplet in schedule order, its
+ * three rows as in ora_sweep); eps = 1.  Returns the rows visited. */
+int64_t ora_sweep_l2(int64_t n, int sched, int64_t B, const double* winv, double* x,
+                     double* ytri, int64_t max_rows) {
+  walk_t w = {n, 1.0, winv, x, ytri, max_rows, NULL, 0, 0, 0};
+  if (!walk_schedule(&w, sched, B)) return max_rows;
+  return max_rows >= 0 ? max_rows - w.rows_left : 3 * w.count;
+}
+
+/* out[0] = objective of Eq. metricnear squared, sum w (x - d)^2
+ * out[1] = QP primal (1/2) sum w (x - d)^2
+ * out[2] = dual objective y^T A d - (1/2) y^T A W^{-1} A^T y, evaluated through
+ *          A^T y = W (d - x) (the identity Algorithm 1 maintains):
+ *          sum w d (d - x) - (1/2) sum w (d - x)^2
+ * out[3] = out[4] = 0 (no pair rows) */
+void ora_objectives_l2(int64_t n, const double* d, const double* w, const double* x,
+                       double* out) {
+  int64_t P = ch2(n);
+  double sq = 0.0, dd = 0.0;
+  for (int64_t p = 0; p < P; ++p) {
+    double r = x[p] - d[p];
+    sq += w[p] * (r * r);
+    dd += w[p] * (d[p] * (d[p] - x[p]));
+  }
+  out[0] = sq;
+  out[1] = 0.5 * sq;
+  out[2] = dd - 0.5 * sq;
+  out[3] = 0.0;
+  out[4] = 0.0;
+}
