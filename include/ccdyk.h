@@ -48,6 +48,10 @@ extern "C" {
 #define CC_ERR_NOT_CONVERGED 5 /* cc_solve reached max_sweeps */
 #define CC_ERR_UNSUPPORTED 6   /* valid request this build does not serve */
 
+/* Problems (opts.problem). */
+#define CC_PROB_CC 0
+#define CC_PROB_L2 1
+
 /* Visiting orders (Sec. III-B/C).  Every schedule visits each triplet once
  * per sweep; triplets of one phase touch pairwise-disjoint pairs, so a phase
  * runs in parallel with the same result as any serial order of it. */
@@ -113,6 +117,19 @@ typedef struct cc_opts {
   int32_t batch_order;      /* batches: order of the shared work list.  0 =
                                phase-major (phase g of every instance, then
                                the next phase), 1 = instance-major.  Default 0. */
+  int32_t problem;          /* CC_PROB_CC (default): the CC LP of Eq. (mn1)
+                               as Eq. (qp).  CC_PROB_L2: l2 metric nearness,
+                               min sum w (x - d)^2 over the metric rows only
+                               (Eq. metricnear, p = 2), i.e. Eq. (qp) with
+                               eps = 1 (opts.eps is not used), c = -W d: x
+                               starts at d, there are no pair rows and f
+                               stays 0.  FP64 only; no batches, warm start or
+                               cc_set_duals (CC_ERR_UNSUPPORTED).  cc_stats
+                               then report lp_objective = sum w (x - d)^2,
+                               qp_primal = half of it, dual_objective = y^T A
+                               d - (1/2) y^T A W^{-1} A^T y (through A^T y =
+                               W (d - x)), gap = sum w x (x - d); cc_solve
+                               also waits for gap <= tol * qp_primal. */
 } cc_opts;
 
 typedef struct cc_stats {
@@ -270,11 +287,11 @@ int cc_batch_sweep(cc_batch* b, int64_t k);
 int cc_batch_solve(cc_batch* b, double tol, int64_t max_sweeps, int64_t* sweeps_done, int64_t* per_instance);
 
 /* Autotuner: times trial_sweeps batch sweeps (after as many warm-up sweeps)
- * for every tile in {8, 16, 32} and work-list order in {0, 1} on the given
- * instances and writes the fastest options (base with tile and batch_order
- * replaced) to *best, its time per sweep in ms to *best_ms (nullable).  The
- * tile changes the visiting order, hence the iterates; only sweep time is
- * compared. */
+ * for every tile in {8, 16, 32}, work-list order in {0, 1} and, in FP64,
+ * variant in {0, 1} on the given instances and writes the fastest options
+ * (base with tile, batch_order and variant replaced) to *best, its time per
+ * sweep in ms to *best_ms (nullable).  The tile changes the visiting order,
+ * hence the iterates; only sweep time is compared. */
 int cc_batch_autotune(int32_t count, const int64_t* ns, const double* const* ds, const double* const* ws,
                       const cc_opts* base, int32_t trial_sweeps, cc_opts* best, double* best_ms);
 

@@ -85,6 +85,28 @@ def batch_planted(count: int, n_lo: int, n_hi: int, k_lo: int, k_hi: int,
     return out
 
 
+def random_dissimilarity(n: int, seed: int, weights=None):
+    """Dissimilarities d_ij ~ U[0, 1] drawn in packed order from
+    default_rng(seed) (a classic metric nearness input: about a sixth of the
+    metric rows start violated); weights as in _finish.  Returns (d, w)."""
+    P = n * (n - 1) // 2
+    d = np.random.default_rng(seed).random(P)
+    w = np.ones(P) if weights is None else np.random.default_rng(seed + 1).uniform(weights[0], weights[1], P)
+    return d, w
+
+
+def noisy_euclidean(n: int, dim: int, noise: float, seed: int):
+    """Distances of n points uniform in [0, 1]^dim, each multiplied by
+    (1 + noise * u), u ~ U[-1, 1] (points first, then one u per pair in
+    packed order, from default_rng(seed)); unit weights.  Returns (d, w)."""
+    rng = np.random.default_rng(seed)
+    pts = rng.random((n, dim))
+    iu, ju = _pairs(n)
+    dist = np.sqrt(((pts[iu] - pts[ju]) ** 2).sum(1))
+    d = dist * (1.0 + noise * rng.uniform(-1.0, 1.0, len(iu)))
+    return d, np.ones(len(iu))
+
+
 # Named workloads (sizes of the paper-shaped synthetic inputs).
 def workload(name: str):
     """Return (n, d, w, description) for a named workload."""

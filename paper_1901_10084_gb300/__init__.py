@@ -28,6 +28,7 @@ __all__ = [
 ]
 
 SCHEDULES = {"diagonal": CC_SCHED_DIAGONAL, "summod": CC_SCHED_SUMMOD, "tiled": CC_SCHED_TILED}
+PROBLEMS = {"cc": _native.CC_PROB_CC, "l2": _native.CC_PROB_L2}
 PRECISIONS = {"fp64": CC_PREC_FP64, "fp32_refine": CC_PREC_FP32_REFINE}
 
 
@@ -59,7 +60,9 @@ class _TorchAllocator:
 
 
 class Solver:
-    """One correlation-clustering LP instance on one GPU.
+    """One correlation-clustering LP instance (``problem="cc"``) or one l2
+    metric nearness instance (``problem="l2"``: min sum w (x - d)^2 over the
+    triangle inequalities) on one GPU.
 
     ``d`` and ``w`` are the packed pair arrays (P = n(n-1)/2 doubles, row-major
     over i<j).  ``stream`` is a ``torch.cuda.Stream`` (default: the current
@@ -70,8 +73,9 @@ class Solver:
     def __init__(self, n, d, w, eps=0.2, schedule="tiled", tile=16, precision="fp64",
                  exact=False, check_every=10, device=0, stream=None, torch_alloc=True,
                  barrier_timeout_s=2.0, grid=0, debug_skip_cta=-1, on_device=False, variant=0,
-                 refine_at=1e-5, trace=False, interleave=True):
+                 refine_at=1e-5, trace=False, interleave=True, problem="cc"):
         o = cc_opts_default()
+        o.problem = PROBLEMS[problem] if isinstance(problem, str) else int(problem)
         o.eps = float(eps)
         o.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
         o.tile = int(tile)
@@ -202,7 +206,7 @@ class Batch:
     a Solver view of instance i (get_x, get_duals, check, set_state ...)."""
 
     def __init__(self, instances, eps=0.2, tile=16, precision="fp64", check_every=10, device=0,
-                 stream=None, torch_alloc=True, interleave=True, batch_order=0, grid=0):
+                 stream=None, torch_alloc=True, interleave=True, batch_order=0, grid=0, variant=0):
         import torch
         o = cc_opts_default()
         o.eps = float(eps)
@@ -213,6 +217,7 @@ class Batch:
         o.interleave = 1 if interleave else 0
         o.batch_order = int(batch_order)
         o.grid = int(grid)
+        o.variant = int(variant)
         if stream is None:
             stream = torch.cuda.current_stream(device)
         o.stream = ctypes.c_void_p(int(stream.cuda_stream))
@@ -260,7 +265,7 @@ class Batch:
 
 
 def autotune_batch(instances, trial_sweeps=5, **kw):
-    """Pick tile and work-list order for a batch by timing trial sweeps;
+    """Pick tile, work-list order and (FP64) sweep form for a batch by timing trial sweeps;
     returns (options dict for Batch, ms per sweep)."""
     import torch
     o = cc_opts_default()
@@ -271,4 +276,4 @@ def autotune_batch(instances, trial_sweeps=5, **kw):
     o.stream = ctypes.c_void_p(int(stream.cuda_stream))
     best, ms = _native.cc_batch_autotune([n for n, _, _ in instances], [d for _, d, _ in instances],
                                          [w for _, _, w in instances], o, trial_sweeps)
-    return {"tile": best.tile, "batch_order": best.batch_order}, ms
+    return {"tile": best.tile, "batch_order": best.batch_order, "variant": best.variant}, ms

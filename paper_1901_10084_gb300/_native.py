@@ -27,6 +27,9 @@ CC_SCHED_TILED = 2
 CC_PREC_FP64 = 0
 CC_PREC_FP32_REFINE = 1
 
+CC_PROB_CC = 0
+CC_PROB_L2 = 1
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -52,6 +55,7 @@ class cc_opts(ctypes.Structure):
         ("trace", ctypes.c_int32),
         ("interleave", ctypes.c_int32),
         ("batch_order", ctypes.c_int32),
+        ("problem", ctypes.c_int32),
     ]
 
 

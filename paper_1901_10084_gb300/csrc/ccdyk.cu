@@ -235,6 +235,7 @@ TiledArgs<T> tiled_args(cc_handle* h) {
   a.work = nullptr;
   a.nbt = h->nbt;
   a.trace = h->trace;
+  a.pairs = h->o.problem == CC_PROB_CC ? 1 : 0;
   a.compact = h->o.variant == 1 ? 1 : 0;
   a.nofilter = h->o.variant == 4 ? 1 : 0;
   return a;
@@ -483,8 +484,14 @@ int read_ctl_error(cc_handle* h) {
 template <typename T>
 int init_state(cc_handle* h) {
   const int th = 256;
-  k_fill<T><<<grid_for(h, h->tile_elems, th), th, 0, h->st>>>((T*)h->x, h->tile_elems, T(0));
-  k_fill<T><<<grid_for(h, h->tile_elems, th), th, 0, h->st>>>((T*)h->f, h->tile_elems, (T)(-1.0 / h->o.eps));
+  if (h->o.problem == CC_PROB_L2) {
+    // Algorithm 1's start -(1/eps) W^{-1} c = d for c = -W d, eps = 1 (FP64 state only)
+    CK(h, cudaMemcpyAsync(h->x, h->d64, (size_t)h->tile_elems * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    k_fill<T><<<grid_for(h, h->tile_elems, th), th, 0, h->st>>>((T*)h->f, h->tile_elems, T(0));
+  } else {
+    k_fill<T><<<grid_for(h, h->tile_elems, th), th, 0, h->st>>>((T*)h->x, h->tile_elems, T(0));
+    k_fill<T><<<grid_for(h, h->tile_elems, th), th, 0, h->st>>>((T*)h->f, h->tile_elems, (T)(-1.0 / h->o.eps));
+  }
   CK(h, cudaMemsetAsync(h->zt, 0, (size_t)h->zt_elems * sizeof(T), h->st));
   CK(h, cudaMemsetAsync(h->zp, 0, (size_t)h->ntiles * 2 * h->B * h->B * sizeof(T), h->st));
   CK(h, cudaGetLastError());
@@ -592,6 +599,9 @@ int check_opts(const cc_opts& o) {
   if (o.variant < 0 || o.variant > 4) return fail(nullptr, CC_ERR_ARG, "variant must be 0..4");
   if (!(o.barrier_timeout_s > 0.0)) return fail(nullptr, CC_ERR_ARG, "barrier_timeout_s must be > 0");
   if ((o.alloc == nullptr) != (o.free == nullptr)) return fail(nullptr, CC_ERR_ARG, "alloc and free go together");
+  if (o.problem != CC_PROB_CC && o.problem != CC_PROB_L2) return fail(nullptr, CC_ERR_ARG, "unknown problem");
+  if (o.problem == CC_PROB_L2 && o.precision != CC_PREC_FP64)
+    return fail(nullptr, CC_ERR_UNSUPPORTED, "l2 metric nearness runs in FP64");
   return CC_OK;
 }
 
@@ -608,6 +618,7 @@ int new_handle(cc_handle** out, int64_t n, const cc_opts* opts, cc_handle** hp) 
   cc_handle* h = new (std::nothrow) cc_handle();
   if (!h) return fail(nullptr, CC_ERR_OOM, "handle");
   h->o = o;
+  if (o.problem == CC_PROB_L2) h->o.eps = 1.0;   // Eq. qp with eps = 1, c = -W d
   h->st = (cudaStream_t)o.stream;
   h->dev = o.device;
   cudaError_t e = cudaSetDevice(h->dev);
@@ -706,6 +717,7 @@ void cc_opts_default(cc_opts* o) {
   o->trace = 0;
   o->interleave = 1;
   o->batch_order = 0;
+  o->problem = CC_PROB_CC;
 }
 
 int cc_create_device(cc_handle** out, int64_t n, const double* d_dev, const double* w_dev, const cc_opts* opts) {
@@ -796,7 +808,8 @@ int check_launch(cc_handle* h) {
                                                                     h->bt_list, h->nbt, pm);                \
   k_pairsums_tiled<T, BV><<<gpair, 256, 0, h->st>>>((const T*)h->x, (const T*)h->f, h->d64,                 \
                                                     h->winv64, (const T*)h->zp, h->tile_list,              \
-                                                    h->ntiles, (int)h->n, yscale, ps);
+                                                    h->ntiles, (int)h->n, yscale,                \
+                                                    h->o.problem == CC_PROB_L2 ? 1 : 0, ps);
   if (h->fp32) {
     if (B == 8) { LAUNCH_CHECK(float, 8) } else if (B == 16) { LAUNCH_CHECK(float, 16) } else { LAUNCH_CHECK(float, 32) }
   } else {
@@ -828,10 +841,19 @@ void check_finish(cc_handle* h, cc_stats* st) {
   s.state_fp32 = h->fp32 ? 1 : 0;
   s.max_violation = mv;
   s.pair_violation = pv;
-  s.lp_objective = lp;
-  s.wf = wf;
-  s.qp_primal = wf + 0.5 * h->o.eps * quad;
-  s.dual_objective = -by - 0.5 * h->o.eps * quad;
+  if (h->o.problem == CC_PROB_L2) {
+    // lp = sum w (x - d)^2, wf = sum w d (d - x); dual through A^T y = W (d - x)
+    s.lp_objective = lp;
+    s.wf = 0.0;
+    s.pair_violation = 0.0;
+    s.qp_primal = 0.5 * lp;
+    s.dual_objective = wf - 0.5 * lp;
+  } else {
+    s.lp_objective = lp;
+    s.wf = wf;
+    s.qp_primal = wf + 0.5 * h->o.eps * quad;
+    s.dual_objective = -by - 0.5 * h->o.eps * quad;
+  }
   s.gap = s.qp_primal - s.dual_objective;
   if (h->ev_recorded) {
     float ms = 0;
@@ -873,7 +895,11 @@ int cc_solve(cc_handle* h, double tol, int64_t max_sweeps, int64_t* sweeps_done)
     rc = cc_check(h, &s);
     if (rc) return rc;
     if (!h->fp32) {
-      if (s.max_violation <= tol) return CC_OK;
+      // l2 nearness also needs the gap closed: Dykstra's iterate is often
+      // feasible long before it is optimal (gap = sum w x (x - d) >= 0 at the optimum)
+      if (s.max_violation <= tol &&
+          (h->o.problem != CC_PROB_L2 || std::fabs(s.gap) <= tol * std::max(s.qp_primal, 1e-300)))
+        return CC_OK;
       continue;
     }
     // FP32 bulk phase: refine in FP64 (from the converted duals) once the
@@ -1022,8 +1048,8 @@ int cc_refine_fp64(cc_handle* h) {
 int cc_set_duals(cc_handle* h, const double* y_tri, const double* y_pair) {
   if (!h) return fail(nullptr, CC_ERR_ARG, "handle is NULL");
   if (!y_tri || !y_pair) return fail(h, CC_ERR_ARG, "y_tri and y_pair are required");
-  if (h->o.schedule != CC_SCHED_TILED || h->o.exact || h->fp32)
-    return fail(h, CC_ERR_UNSUPPORTED, "cc_set_duals needs the tiled schedule, fused form, FP64 state");
+  if (h->o.schedule != CC_SCHED_TILED || h->o.exact || h->fp32 || h->o.problem != CC_PROB_CC)
+    return fail(h, CC_ERR_UNSUPPORTED, "cc_set_duals needs the CC problem, tiled schedule, fused form, FP64 state");
   CK(h, cudaSetDevice(h->dev));
   int rc = read_ctl_error(h);
   if (rc) return rc;
@@ -1271,6 +1297,7 @@ int cc_batch_create(cc_batch** out, int32_t count, const int64_t* ns, const doub
   if (opts) o = *opts;
   if (o.schedule != CC_SCHED_TILED || o.exact)
     return bfail(nullptr, CC_ERR_ARG, "a batch runs the tiled schedule in the fused form");
+  if (o.problem != CC_PROB_CC) return bfail(nullptr, CC_ERR_UNSUPPORTED, "a batch holds CC instances");
   cc_batch* b = new (std::nothrow) cc_batch();
   if (!b) return bfail(nullptr, CC_ERR_OOM, "batch");
   b->o = o;
@@ -1389,11 +1416,14 @@ int cc_batch_autotune(int32_t count, const int64_t* ns, const double* const* ds,
   const int tiles[3] = {8, 16, 32};
   double best_t = INFINITY;
   cc_opts pick = o;
+  const int nvar = o.precision == CC_PREC_FP64 ? 2 : 1;   // variant 1 differs from 0 in FP64 only
   for (int ti = 0; ti < 3; ++ti)
-    for (int order = 0; order < 2; ++order) {
+    for (int order = 0; order < 2; ++order)
+    for (int var = 0; var < nvar; ++var) {
       cc_opts c = o;
       c.tile = tiles[ti];
       c.batch_order = order;
+      c.variant = var;
       cc_batch* b = nullptr;
       int rc = cc_batch_create(&b, count, ns, ds, ws, &c);
       if (rc) return rc;
@@ -1501,7 +1531,7 @@ void ws_release(cc_handle* h, WsCands& c) {
 }
 
 bool ws_usable(const cc_handle* h) {
-  return h->o.schedule == CC_SCHED_TILED && !h->o.exact && !h->fp32 && h->mask;
+  return h->o.schedule == CC_SCHED_TILED && !h->o.exact && !h->fp32 && h->mask && h->o.problem == CC_PROB_CC;
 }
 
 }  // namespace

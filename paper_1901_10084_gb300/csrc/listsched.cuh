@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256) k_sweep_summod(TiledArgs<T> a, ListArgs L
     const bool skip = (s == 0) && ((int)blockIdx.x == a.skip_cta);
     if (!grid_barrier(a.ctl, target, a.timeout_ns, s, skip, &s_flag)) return;
   }
-  list_pair_phase<T, EXACT>(a, L.B);
+  if (a.pairs) list_pair_phase<T, EXACT>(a, L.B);
 }
 
 template <typename T, bool EXACT, bool UNITW>
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256) k_sweep_diagonal(TiledArgs<T> a, ListArgs
     const bool skip = (p == 0) && ((int)blockIdx.x == a.skip_cta);
     if (!grid_barrier(a.ctl, target, a.timeout_ns, p, skip, &s_flag)) return;
   }
-  list_pair_phase<T, EXACT>(a, L.B);
+  if (a.pairs) list_pair_phase<T, EXACT>(a, L.B);
 }
 
 // Triangle duals between the schedule-0/1 store and canonical order.

@@ -52,6 +52,7 @@ struct TiledArgs {
   int nbt;              // block triples per sweep
   unsigned long long* trace;  // optional per-item timestamps (nullptr = off)
   int* cnt;             // per-tile visit counters of this instance (batched sweep)
+  int pairs;            // 1: the pair rows of the CC LP follow the metric rows; 0: l2 nearness
   int compact;          // FP64 CTA items: 1 = compacted update lists per sub-phase
   int nofilter;         // 1: update every triplet and row (reference for the filters)
 };
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(TileCfg<B>::NT) k_sweep_tiled(TiledArgs<T> a) 
     const bool skip = (g == 0) && ((int)blockIdx.x == a.skip_cta);
     if (!grid_barrier(a.ctl, target, a.timeout_ns, g, skip, &s_flag)) return;
   }
-  tiled_pair_phase<T, EXACT, B>(a);
+  if (a.pairs) tiled_pair_phase<T, EXACT, B>(a);
 }
 
 // ------------------------------------------------------------ filtered sweep
@@ -829,7 +830,7 @@ __global__ void __launch_bounds__(NT) k_sweep_flow(TiledArgs<T> a, int* flow) {
   FlowSmem<T, B>& sm = *reinterpret_cast<FlowSmem<T, B>*>(smem_raw);
   int* const next = flow;            // item counter
   int* const tile_cnt = flow + 1;    // visits per tile in this sweep
-  const int total = a.nbt + a.ntiles;
+  const int total = a.nbt + (a.pairs ? a.ntiles : 0);
   bool first = true;
   if (threadIdx.x == 0) sm.item = atomicAdd(next, 1);
   __syncthreads();
@@ -931,7 +932,7 @@ __global__ void __launch_bounds__(256) k_sweep_warpflow(TiledArgs<T> a, int* flo
   FlowSmem<T, B>& sm = reinterpret_cast<FlowSmem<T, B>*>(smem_raw)[wid];
   int* const next = flow;
   int* const tile_cnt = flow + 1;
-  const int total = a.nbt + a.ntiles;
+  const int total = a.nbt + (a.pairs ? a.ntiles : 0);
   bool first = true;
   while (true) {
     int w = 0;
@@ -1073,7 +1074,7 @@ template <typename T, int B>
 __global__ void __launch_bounds__(256) k_pairsums_tiled(const T* __restrict__ x, const T* __restrict__ f,
                                                          const double* __restrict__ d, const double* __restrict__ winv,
                                                          const T* __restrict__ zp, const int* __restrict__ tile_list,
-                                                         int ntiles, int n, double yscale, double* part) {
+                                                         int ntiles, int n, double yscale, int l2, double* part) {
   using C = TileCfg<B>;
   __shared__ double sred[32];
   double lp = 0, wf = 0, quad = 0, by = 0, pv = 0;
@@ -1086,6 +1087,11 @@ __global__ void __launch_bounds__(256) k_pairsums_tiled(const T* __restrict__ x,
     const int la = slot / B, lb = slot % B;
     if (!((I < J || la < lb) && J * B + lb < n)) continue;
     const double xv = x[e], fv = f[e], dv = d[e], wv = 1.0 / winv[e];
+    if (l2) {   // sum w (x - d)^2 and sum w d (d - x)
+      lp += wv * ((xv - dv) * (xv - dv));
+      wf += wv * (dv * (dv - xv));
+      continue;
+    }
     const double yp = yscale * (double)zp[(int64_t)tl * 2 * C::BB + slot];
     const double ym = yscale * (double)zp[(int64_t)tl * 2 * C::BB + C::BB + slot];
     lp += wv * fabs(xv - dv);

@@ -67,7 +67,7 @@ def test_autotuner_returns_a_valid_choice():
     import paper_1901_10084_gb300 as cc
     inst = batch_planted(6, 30, 90, 2, 5, 0.7, 0.05, seed=2)
     opts, ms = cc.autotune_batch(inst, trial_sweeps=2)
-    assert opts["tile"] in (8, 16, 32) and opts["batch_order"] in (0, 1) and ms > 0
+    assert opts["tile"] in (8, 16, 32) and opts["batch_order"] in (0, 1) and opts["variant"] in (0, 1) and ms > 0
     with cc.Batch(inst, **opts) as b:
         conv, _, _ = b.solve(1e-4, 3000)
         assert conv
