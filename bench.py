@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
     p.add_argument("--batch-count", type=int, default=256)
     p.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start measurement")
+    p.add_argument("--no-l2", action="store_true", help="skip the l2 metric nearness measurement")
     p.add_argument("--ws-train-count", type=int, default=2000,
                    help="Chung-Lu n=200 training instances for the warm-start network")
     p.add_argument("--ws-steps", type=int, default=3000)
@@ -252,6 +253,8 @@ def run_ours(args, rank, world, local_rank):
         out["batched_form"] = _batched(args, stream)
     if rank == 0 and not args.no_warm_start and args.schedule == "tiled":
         out["warm_start"] = _warm_start(args, stream)
+    if rank == 0 and not args.no_l2 and args.schedule == "tiled":
+        out["l2_nearness"] = _l2(args, stream)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -355,6 +358,42 @@ def _warm_start(args, stream):
                            "lp_objective": s.check()["lp_objective"]}
         r["speedup"] = r["cold"]["seconds"] / r["warm"]["seconds"]
         rec[name] = r
+    return rec
+
+
+def _l2(args, stream):
+    """l2 metric nearness (min sum w (x - d)^2 over the triangle inequalities)
+    at n = 1000, FP64, tiled B = 16: U[0,1] dissimilarities (seed 1) and noisy
+    Euclidean distances (2-D points, noise 0.3, seed 1).  Sweep rate over 20
+    sweeps after 3; time to violation <= tol with the gap <= tol relative."""
+    import torch
+
+    import paper_1901_10084_gb300 as cc
+    from instances import noisy_euclidean, random_dissimilarity
+    n = 1000
+    T = n * (n - 1) * (n - 2) // 6
+    rec = {}
+    for name, (d, w), cap in (("random_u01_n1000", random_dissimilarity(n, 1), 2000),
+                              ("noisy_euclidean_n1000", noisy_euclidean(n, 2, 0.3, 1), 5000)):
+        with cc.Solver(n, d, w, problem="l2", tile=args.tile, stream=stream) as s:
+            s.sweep(3)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.sweep(20)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 20
+        with cc.Solver(n, d, w, problem="l2", tile=args.tile, check_every=args.check_every, stream=stream) as s:
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            ok, k = s.solve(args.tol, cap)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t
+            st = s.check()
+        rec[name] = {"sweep_ms": ms, "value": T / (ms * 1e-3), "unit": UNIT,
+                     "time_to_tol": {"seconds": el, "sweeps": k, "converged": ok, "tol": args.tol,
+                                     "max_violation": st["max_violation"], "objective": st["lp_objective"],
+                                     "gap_rel": st["gap"] / st["qp_primal"] if st["qp_primal"] else 0.0}}
     return rec
 
 

@@ -48,6 +48,10 @@ extern "C" {
 #define CC_ERR_NOT_CONVERGED 5 /* cc_solve reached max_sweeps */
 #define CC_ERR_UNSUPPORTED 6   /* valid request this build does not serve */
 
+/* Dual stores (opts.store). */
+#define CC_STORE_DENSE 0
+#define CC_STORE_SPARSE 1
+
 /* Problems (opts.problem). */
 #define CC_PROB_CC 0
 #define CC_PROB_L2 1
@@ -130,6 +134,23 @@ typedef struct cc_opts {
                                d - (1/2) y^T A W^{-1} A^T y (through A^T y =
                                W (d - x)), gap = sum w x (x - d); cc_solve
                                also waits for gap <= tol * qp_primal. */
+  int32_t store;            /* CC_STORE_DENSE (default): triangle duals dense
+                               in schedule order plus a nonzero-dual bitmask,
+                               O(n^3) memory.  CC_STORE_SPARSE: the
+                               per-processor sparse store of Sec. III-D, per
+                               block triple a list of its nonzero duals
+                               (local index, value) in visiting order, so
+                               memory is O(n^2 + nonzero duals).  Needs the
+                               tiled schedule, fused form, FP64 and variant
+                               0, 3 or 4; duals can be read (cc_get_duals)
+                               but not set (cc_set_state, cc_set_duals,
+                               warm start: CC_ERR_UNSUPPORTED); no batches.
+                               Same values as the dense store. */
+  int64_t pool_entries;     /* sparse store: initial capacity of each of the
+                               two entry pools (0 = max(2^20, 4 x block
+                               triples)).  A sweep whose next pool overflows
+                               is undone and run again with the pool grown to
+                               1.5 x the entries it needed. */
 } cc_opts;
 
 typedef struct cc_stats {
@@ -144,6 +165,10 @@ typedef struct cc_stats {
   double last_sweep_ms;    /* device time of the most recent sweep launch */
   int64_t fp32_sweeps;     /* sweeps run with FP32 state (CC_PREC_FP32_REFINE) */
   int32_t state_fp32;      /* 1 while the state is held in FP32 */
+  int64_t dual_nnz;        /* sparse store: triangle duals held (entries of
+                              the current pool); -1 with the dense store */
+  int64_t pool_retries;    /* sparse store: sweeps undone and run again after
+                              the next pool grew */
 } cc_stats;
 
 typedef struct cc_handle cc_handle;

@@ -29,6 +29,7 @@ __all__ = [
 
 SCHEDULES = {"diagonal": CC_SCHED_DIAGONAL, "summod": CC_SCHED_SUMMOD, "tiled": CC_SCHED_TILED}
 PROBLEMS = {"cc": _native.CC_PROB_CC, "l2": _native.CC_PROB_L2}
+STORES = {"dense": _native.CC_STORE_DENSE, "sparse": _native.CC_STORE_SPARSE}
 PRECISIONS = {"fp64": CC_PREC_FP64, "fp32_refine": CC_PREC_FP32_REFINE}
 
 
@@ -73,9 +74,12 @@ class Solver:
     def __init__(self, n, d, w, eps=0.2, schedule="tiled", tile=16, precision="fp64",
                  exact=False, check_every=10, device=0, stream=None, torch_alloc=True,
                  barrier_timeout_s=2.0, grid=0, debug_skip_cta=-1, on_device=False, variant=0,
-                 refine_at=1e-5, trace=False, interleave=True, problem="cc"):
+                 refine_at=1e-5, trace=False, interleave=True, problem="cc", store="dense",
+                 pool_entries=0):
         o = cc_opts_default()
         o.problem = PROBLEMS[problem] if isinstance(problem, str) else int(problem)
+        o.store = STORES[store] if isinstance(store, str) else int(store)
+        o.pool_entries = int(pool_entries)
         o.eps = float(eps)
         o.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
         o.tile = int(tile)

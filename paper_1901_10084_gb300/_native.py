@@ -30,6 +30,9 @@ CC_PREC_FP32_REFINE = 1
 CC_PROB_CC = 0
 CC_PROB_L2 = 1
 
+CC_STORE_DENSE = 0
+CC_STORE_SPARSE = 1
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -56,6 +59,8 @@ class cc_opts(ctypes.Structure):
         ("interleave", ctypes.c_int32),
         ("batch_order", ctypes.c_int32),
         ("problem", ctypes.c_int32),
+        ("store", ctypes.c_int32),
+        ("pool_entries", ctypes.c_int64),
     ]
 
 
@@ -72,6 +77,8 @@ class cc_stats(ctypes.Structure):
         ("last_sweep_ms", ctypes.c_double),
         ("fp32_sweeps", ctypes.c_int64),
         ("state_fp32", ctypes.c_int32),
+        ("dual_nnz", ctypes.c_int64),
+        ("pool_retries", ctypes.c_int64),
     ]
 
     def as_dict(self) -> dict:

@@ -60,6 +60,20 @@ struct cc_handle {
   int* flow = nullptr;       // dataflow sweep: item counter + visits per tile
   unsigned long long* trace = nullptr;   // per-item timestamps of the last sweep (opts.trace)
   int* lab = nullptr;        // caller label -> internal label (tiled schedule, opts.interleave)
+  int* ilab = nullptr;       // internal label -> caller label (sparse store export)
+  // sparse dual store (opts.store = CC_STORE_SPARSE): two pools of entries
+  bool sparse = false;
+  uint32_t* sp_idx[2] = {nullptr, nullptr};
+  double* sp_val[2] = {nullptr, nullptr};
+  long long* sp_off[2] = {nullptr, nullptr};
+  int* sp_cnt[2] = {nullptr, nullptr};
+  int64_t sp_cap[2] = {0, 0};
+  int sp_cur = 0;            // pool read by the next sweep
+  unsigned long long* sp_top = nullptr;
+  double* sp_scratch = nullptr;   // 3 B^3 doubles per CTA of the sweep
+  double* snap = nullptr;    // x, f, pair duals before a sparse sweep
+  int64_t sp_nnz = 0;        // entries in the current pool
+  int64_t sp_retries = 0;    // sweeps run again after the next pool grew
   std::vector<int> h_bt_off; // host copy of the phase offsets of the block triples
   // schedules 0 and 1 (device tables)
   ListArgs la{};
@@ -238,6 +252,33 @@ TiledArgs<T> tiled_args(cc_handle* h) {
   a.pairs = h->o.problem == CC_PROB_CC ? 1 : 0;
   a.compact = h->o.variant == 1 ? 1 : 0;
   a.nofilter = h->o.variant == 4 ? 1 : 0;
+  a.sparse = h->sparse ? 1 : 0;
+  if (h->sparse) {
+    const int c = h->sp_cur, nx = 1 - c;
+    a.sp_idx = h->sp_idx[c];
+    a.sp_val = (const T*)h->sp_val[c];
+    a.sp_off = h->sp_off[c];
+    a.sp_cnt = h->sp_cnt[c];
+    a.sp_idx_next = h->sp_idx[nx];
+    a.sp_val_next = (T*)h->sp_val[nx];
+    a.sp_off_next = h->sp_off[nx];
+    a.sp_cnt_next = h->sp_cnt[nx];
+    a.sp_top = h->sp_top;
+    a.sp_cap = (long long)h->sp_cap[nx];
+    a.sp_scratch = (T*)h->sp_scratch;
+  } else {
+    a.sp_idx = nullptr;
+    a.sp_val = nullptr;
+    a.sp_off = nullptr;
+    a.sp_cnt = nullptr;
+    a.sp_idx_next = nullptr;
+    a.sp_val_next = nullptr;
+    a.sp_off_next = nullptr;
+    a.sp_cnt_next = nullptr;
+    a.sp_top = nullptr;
+    a.sp_cap = 0;
+    a.sp_scratch = nullptr;
+  }
   return a;
 }
 
@@ -272,6 +313,52 @@ int configure_sweep(cc_handle* h) {
   return CC_OK;
 }
 
+int read_ctl_error(cc_handle* h);
+
+// One sweep with the sparse store: the current pool is only read, so a sweep
+// whose next pool overflows is undone (x, f and the pair duals back from the
+// snapshot), the next pool grows to the size the sweep reported, and the sweep
+// runs again.  Synchronizes once per sweep.
+int sweep_sparse(cc_handle* h) {
+  const size_t te = (size_t)h->tile_elems * sizeof(double);
+  void* k = sweep_kernel(h);
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    CK(h, cudaMemcpyAsync(h->snap, h->x, te, cudaMemcpyDeviceToDevice, h->st));
+    CK(h, cudaMemcpyAsync(h->snap + h->tile_elems, h->f, te, cudaMemcpyDeviceToDevice, h->st));
+    CK(h, cudaMemcpyAsync(h->snap + 2 * h->tile_elems, h->zp, 2 * te, cudaMemcpyDeviceToDevice, h->st));
+    CK(h, cudaMemsetAsync(h->sp_top, 0, sizeof(unsigned long long), h->st));
+    CK(h, cudaMemsetAsync(h->flow, 0, (size_t)(1 + h->ntiles) * sizeof(int), h->st));
+    int* flow = h->flow;
+    TiledArgs<double> a = tiled_args<double>(h);
+    void* args[] = {&a, &flow};
+    CK(h, cudaLaunchCooperativeKernel(k, h->sweep_grid, h->sweep_threads, args, h->dyn_smem, h->st));
+    unsigned long long top = 0;
+    CK(h, cudaMemcpyAsync(&top, h->sp_top, sizeof top, cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    const int nx = 1 - h->sp_cur;
+    if (top <= (unsigned long long)h->sp_cap[nx]) {
+      h->sp_cur = nx;
+      h->sp_nnz = (int64_t)top;
+      return CC_OK;
+    }
+    int rc = read_ctl_error(h);
+    if (rc) return rc;
+    CK(h, cudaMemcpyAsync(h->x, h->snap, te, cudaMemcpyDeviceToDevice, h->st));
+    CK(h, cudaMemcpyAsync(h->f, h->snap + h->tile_elems, te, cudaMemcpyDeviceToDevice, h->st));
+    CK(h, cudaMemcpyAsync(h->zp, h->snap + 2 * h->tile_elems, 2 * te, cudaMemcpyDeviceToDevice, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    dfree(h, h->sp_idx[nx]);
+    dfree(h, h->sp_val[nx]);
+    const int64_t cap = (int64_t)top + (int64_t)top / 2 + 1024;
+    h->sp_idx[nx] = (uint32_t*)dalloc(h, (size_t)cap * sizeof(uint32_t));
+    h->sp_val[nx] = (double*)dalloc(h, (size_t)cap * sizeof(double));
+    if (!h->sp_idx[nx] || !h->sp_val[nx]) return fail(h, CC_ERR_OOM, "sparse dual pool");
+    h->sp_cap[nx] = cap;
+    ++h->sp_retries;
+  }
+  return fail(h, CC_ERR_OOM, "sparse dual pool keeps overflowing");
+}
+
 int launch_sweep(cc_handle* h) {
   void* k = sweep_kernel(h);
   if (h->o.schedule != CC_SCHED_TILED) {
@@ -295,6 +382,7 @@ int launch_sweep(cc_handle* h) {
     CK(h, cudaLaunchCooperativeKernel(k, h->sweep_grid, h->sweep_threads, args, 0, h->st));
     return CC_OK;
   }
+  if (h->sparse) return sweep_sparse(h);
   CK(h, cudaMemsetAsync(h->flow, 0, (size_t)(1 + h->ntiles) * sizeof(int), h->st));
   int* flow = h->flow;
   if (h->fp32) {
@@ -498,6 +586,41 @@ int init_state(cc_handle* h) {
   return CC_OK;
 }
 
+// Sparse store: two pools (entries), their tables, the per-CTA scratch
+// blocks (zero), the snapshot for undoing a sweep, and the inverse labels.
+int alloc_sparse(cc_handle* h) {
+  const int64_t cap = h->o.pool_entries > 0 ? h->o.pool_entries : std::max<int64_t>((int64_t)1 << 20, 4 * (int64_t)h->nbt);
+  for (int p = 0; p < 2; ++p) {
+    h->sp_idx[p] = (uint32_t*)dalloc(h, (size_t)cap * sizeof(uint32_t));
+    h->sp_val[p] = (double*)dalloc(h, (size_t)cap * sizeof(double));
+    h->sp_off[p] = (long long*)dalloc(h, (size_t)h->nbt * sizeof(long long));
+    h->sp_cnt[p] = (int*)dalloc(h, (size_t)h->nbt * sizeof(int));
+    if (!h->sp_idx[p] || !h->sp_val[p] || !h->sp_off[p] || !h->sp_cnt[p]) return fail(h, CC_ERR_OOM, "sparse dual pools");
+    h->sp_cap[p] = cap;
+    CK(h, cudaMemsetAsync(h->sp_cnt[p], 0, (size_t)h->nbt * sizeof(int), h->st));
+    CK(h, cudaMemsetAsync(h->sp_off[p], 0, (size_t)h->nbt * sizeof(long long), h->st));
+  }
+  const size_t scratch = (size_t)h->sweep_grid * 3 * h->B * h->B * h->B;
+  h->sp_scratch = (double*)dalloc(h, scratch * sizeof(double));
+  h->sp_top = (unsigned long long*)dalloc(h, sizeof(unsigned long long));
+  h->snap = (double*)dalloc(h, (size_t)h->tile_elems * 4 * sizeof(double));
+  if (!h->sp_scratch || !h->sp_top || !h->snap) return fail(h, CC_ERR_OOM, "sparse store scratch");
+  CK(h, cudaMemsetAsync(h->sp_scratch, 0, scratch * sizeof(double), h->st));
+  if (h->lab) {
+    std::vector<int> lab((size_t)h->n), inv((size_t)h->n);
+    CK(h, cudaMemcpyAsync(lab.data(), h->lab, (size_t)h->n * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+    for (int64_t i = 0; i < h->n; ++i) inv[(size_t)lab[(size_t)i]] = (int)i;
+    h->ilab = (int*)dalloc(h, (size_t)h->n * sizeof(int));
+    if (!h->ilab) return fail(h, CC_ERR_OOM, "inverse labels");
+    CK(h, cudaMemcpyAsync(h->ilab, inv.data(), (size_t)h->n * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  }
+  CK(h, cudaStreamSynchronize(h->st));
+  h->sp_cur = 0;
+  h->sp_nnz = 0;
+  return CC_OK;
+}
+
 int create_common(cc_handle** out, int64_t n, const double* d_dev, const double* w_dev, const cc_opts* opts,
                   cc_handle* h) {
   h->n = n;
@@ -544,23 +667,26 @@ int create_common(cc_handle** out, int64_t n, const double* d_dev, const double*
     h->winv = h->winv64;
   }
   h->zp = dalloc(h, te * 2 * h->esz);
-  h->zt = dalloc(h, (size_t)h->zt_elems * h->esz);
+  h->sparse = h->o.store == CC_STORE_SPARSE;
+  if (h->sparse) h->zt_elems = 0;
+  else h->zt = dalloc(h, (size_t)h->zt_elems * h->esz);
   h->ctl = (Ctl*)dalloc(h, sizeof(Ctl));
   if (!h->o.exact && h->o.schedule == CC_SCHED_TILED) {
-    h->mask_words = (int64_t)h->nbt * 3 * h->B * ((h->B * h->B) / 32);
-    h->mask = (uint32_t*)dalloc(h, (size_t)h->mask_words * sizeof(uint32_t));
+    h->mask_words = h->sparse ? 0 : (int64_t)h->nbt * 3 * h->B * ((h->B * h->B) / 32);
+    if (!h->sparse) h->mask = (uint32_t*)dalloc(h, (size_t)h->mask_words * sizeof(uint32_t));
     h->flow = (int*)dalloc(h, (size_t)(1 + h->ntiles) * sizeof(int));
     if (h->o.trace) {
       h->trace = (unsigned long long*)dalloc(h, (size_t)(h->nbt + h->ntiles) * 6 * sizeof(unsigned long long));
       if (!h->trace) return fail(h, CC_ERR_OOM, "trace buffer");
       CK(h, cudaMemsetAsync(h->trace, 0, (size_t)(h->nbt + h->ntiles) * 6 * sizeof(unsigned long long), h->st));
     }
-    if (!h->mask || !h->flow) return fail(h, CC_ERR_OOM, "dual bitmask");
-    CK(h, cudaMemsetAsync(h->mask, 0, (size_t)h->mask_words * sizeof(uint32_t), h->st));
+    if ((!h->sparse && !h->mask) || !h->flow) return fail(h, CC_ERR_OOM, "dual bitmask");
+    if (h->mask) CK(h, cudaMemsetAsync(h->mask, 0, (size_t)h->mask_words * sizeof(uint32_t), h->st));
   }
   h->part_cap = std::max(8 * h->sms, 64);
   h->part = (double*)dalloc(h, (size_t)h->part_cap * 6 * sizeof(double));  // maxima, then 5 sums each
-  if (!h->x || !h->f || !h->d64 || !h->winv64 || !h->d || !h->winv || !h->zp || !h->zt || !h->ctl || !h->part)
+  if (!h->x || !h->f || !h->d64 || !h->winv64 || !h->d || !h->winv || !h->zp || (!h->zt && !h->sparse) || !h->ctl ||
+      !h->part)
     return fail(h, CC_ERR_OOM, "device state");
   CK(h, cudaMallocHost((void**)&h->h_pin, (size_t)h->part_cap * 6 * sizeof(double)));
   CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->st));
@@ -580,6 +706,10 @@ int create_common(cc_handle** out, int64_t n, const double* d_dev, const double*
   CK(h, cudaEventCreate(&h->ev1));
   rc = configure_sweep(h);
   if (rc) return rc;
+  if (h->sparse) {
+    rc = alloc_sparse(h);
+    if (rc) return rc;
+  }
   CK(h, cudaStreamSynchronize(h->st));
   *out = h;
   return CC_OK;
@@ -602,6 +732,12 @@ int check_opts(const cc_opts& o) {
   if (o.problem != CC_PROB_CC && o.problem != CC_PROB_L2) return fail(nullptr, CC_ERR_ARG, "unknown problem");
   if (o.problem == CC_PROB_L2 && o.precision != CC_PREC_FP64)
     return fail(nullptr, CC_ERR_UNSUPPORTED, "l2 metric nearness runs in FP64");
+  if (o.store != CC_STORE_DENSE && o.store != CC_STORE_SPARSE) return fail(nullptr, CC_ERR_ARG, "unknown store");
+  if (o.pool_entries < 0) return fail(nullptr, CC_ERR_ARG, "pool_entries must be >= 0");
+  if (o.store == CC_STORE_SPARSE &&
+      (o.schedule != CC_SCHED_TILED || o.exact || o.precision != CC_PREC_FP64 ||
+       (o.variant != 0 && o.variant != 3 && o.variant != 4)))
+    return fail(nullptr, CC_ERR_UNSUPPORTED, "the sparse store runs the tiled schedule, fused form, FP64, variant 0, 3 or 4");
   return CC_OK;
 }
 
@@ -718,6 +854,8 @@ void cc_opts_default(cc_opts* o) {
   o->interleave = 1;
   o->batch_order = 0;
   o->problem = CC_PROB_CC;
+  o->store = CC_STORE_DENSE;
+  o->pool_entries = 0;
 }
 
 int cc_create_device(cc_handle** out, int64_t n, const double* d_dev, const double* w_dev, const cc_opts* opts) {
@@ -838,6 +976,8 @@ void check_finish(cc_handle* h, cc_stats* st) {
   cc_stats& s = h->last;
   s.sweeps = h->sweeps;
   s.fp32_sweeps = h->fp32_sweeps;
+  s.dual_nnz = h->sparse ? h->sp_nnz : -1;
+  s.pool_retries = h->sp_retries;
   s.state_fp32 = h->fp32 ? 1 : 0;
   s.max_violation = mv;
   s.pair_violation = pv;
@@ -942,6 +1082,7 @@ int cc_get_x(cc_handle* h, double* x, double* f) {
 
 static int move_duals(cc_handle* h, double* y_tri, double* y_pair, int64_t first, int64_t count, int dir) {
   const double scale = h->o.exact ? 1.0 : h->o.eps;
+  if (h->sparse && dir == 1 && y_tri) return fail(h, CC_ERR_UNSUPPORTED, "the sparse store does not import duals");
   const int64_t chunk = std::min<int64_t>(std::max<int64_t>(count, 1), (int64_t)1 << 22);
   int rc = ensure_stage(h, std::max<int64_t>(3 * chunk, 2 * h->P));
   if (rc) return rc;
@@ -951,6 +1092,21 @@ static int move_duals(cc_handle* h, double* y_tri, double* y_pair, int64_t first
       if (dir == 1)
         CK(h, cudaMemcpyAsync(h->stage, y_tri + 3 * c0, 3 * m * sizeof(double), cudaMemcpyHostToDevice, h->st));
       const int g = grid_for(h, m, 256);
+      if (h->sparse) {
+        CK(h, cudaMemsetAsync(h->stage, 0, 3 * m * sizeof(double), h->st));
+        const int gw = grid_for(h, h->nbt, 128);
+        const int c = h->sp_cur;
+#define LAUNCH_SP(BV)                                                                                          \
+  k_tri_duals_sparse<BV><<<gw, 128, 0, h->st>>>(h->sp_idx[c], h->sp_val[c], h->sp_off[c], h->sp_cnt[c],        \
+                                               h->bt_list, h->nbt, (int)h->n, h->ilab, first + c0, m, h->stage, \
+                                               scale);
+        if (h->B == 8) { LAUNCH_SP(8) } else if (h->B == 16) { LAUNCH_SP(16) } else { LAUNCH_SP(32) }
+#undef LAUNCH_SP
+        CK(h, cudaGetLastError());
+        CK(h, cudaMemcpyAsync(y_tri + 3 * c0, h->stage, 3 * m * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+        CK(h, cudaStreamSynchronize(h->st));
+        continue;
+      }
       if (h->o.schedule != CC_SCHED_TILED) {
         if (h->fp32)
           k_tri_duals_list<float><<<g, 256, 0, h->st>>>((float*)h->zt, h->la, (int)h->n, first + c0, m, h->stage, scale, dir);
@@ -1005,6 +1161,7 @@ int cc_get_duals(cc_handle* h, double* y_tri, double* y_pair, int64_t tri_first,
 int cc_set_state(cc_handle* h, const double* x, const double* f, const double* y_tri, const double* y_pair) {
   if (!h) return fail(nullptr, CC_ERR_ARG, "handle is NULL");
   if (!x || !f || !y_tri || !y_pair) return fail(h, CC_ERR_ARG, "all four arrays are required");
+  if (h->sparse) return fail(h, CC_ERR_UNSUPPORTED, "the sparse store does not import duals");
   CK(h, cudaSetDevice(h->dev));
   int rc = read_ctl_error(h);
   if (rc) return rc;
@@ -1048,8 +1205,9 @@ int cc_refine_fp64(cc_handle* h) {
 int cc_set_duals(cc_handle* h, const double* y_tri, const double* y_pair) {
   if (!h) return fail(nullptr, CC_ERR_ARG, "handle is NULL");
   if (!y_tri || !y_pair) return fail(h, CC_ERR_ARG, "y_tri and y_pair are required");
-  if (h->o.schedule != CC_SCHED_TILED || h->o.exact || h->fp32 || h->o.problem != CC_PROB_CC)
-    return fail(h, CC_ERR_UNSUPPORTED, "cc_set_duals needs the CC problem, tiled schedule, fused form, FP64 state");
+  if (h->o.schedule != CC_SCHED_TILED || h->o.exact || h->fp32 || h->o.problem != CC_PROB_CC || h->sparse)
+    return fail(h, CC_ERR_UNSUPPORTED,
+                "cc_set_duals needs the CC problem, tiled schedule, fused form, FP64 state, dense store");
   CK(h, cudaSetDevice(h->dev));
   int rc = read_ctl_error(h);
   if (rc) return rc;
@@ -1084,6 +1242,8 @@ int cc_get_stats(cc_handle* h, cc_stats* st) {
   st->sweeps = h->sweeps;
   st->fp32_sweeps = h->fp32_sweeps;
   st->state_fp32 = h->fp32 ? 1 : 0;
+  st->dual_nnz = h->sparse ? h->sp_nnz : -1;
+  st->pool_retries = h->sp_retries;
   return CC_OK;
 }
 
@@ -1298,6 +1458,7 @@ int cc_batch_create(cc_batch** out, int32_t count, const int64_t* ns, const doub
   if (o.schedule != CC_SCHED_TILED || o.exact)
     return bfail(nullptr, CC_ERR_ARG, "a batch runs the tiled schedule in the fused form");
   if (o.problem != CC_PROB_CC) return bfail(nullptr, CC_ERR_UNSUPPORTED, "a batch holds CC instances");
+  if (o.store != CC_STORE_DENSE) return bfail(nullptr, CC_ERR_UNSUPPORTED, "a batch uses the dense store");
   cc_batch* b = new (std::nothrow) cc_batch();
   if (!b) return bfail(nullptr, CC_ERR_OOM, "batch");
   b->o = o;

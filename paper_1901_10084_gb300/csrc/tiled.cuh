@@ -55,6 +55,22 @@ struct TiledArgs {
   int pairs;            // 1: the pair rows of the CC LP follow the metric rows; 0: l2 nearness
   int compact;          // FP64 CTA items: 1 = compacted update lists per sub-phase
   int nofilter;         // 1: update every triplet and row (reference for the filters)
+  // sparse dual store (Sec. III-D): per block triple w, entries
+  // [sp_off[w], sp_off[w] + sp_cnt[w]) of (local index, value), local index =
+  // the dense offset inside the block triple's 3 B^3 slots, ascending; a sweep
+  // reads the current pool and writes the next one (bump allocator sp_top)
+  int sparse;
+  const uint32_t* sp_idx;
+  const T* sp_val;
+  const long long* sp_off;
+  const int* sp_cnt;
+  uint32_t* sp_idx_next;
+  T* sp_val_next;
+  long long* sp_off_next;
+  int* sp_cnt_next;
+  unsigned long long* sp_top;
+  long long sp_cap;     // entries the next pool holds
+  T* sp_scratch;        // 3 B^3 values per CTA, all zero between items
 };
 
 __device__ __forceinline__ void unpack_bt(int pk, int& I, int& J, int& K) {
@@ -325,6 +341,8 @@ struct alignas(16) FlowSmem {
   int lcnt[B];              // list length per sub-phase
   int scan[32];
   int item, flag, total, dirty;
+  uint32_t nmask[MaskCfg<B>::PER_BT];   // sparse store: nonzero-dual bits after the item
+  unsigned long long base;              //   and its place in the next pool
   int ntrip, nrows, nsub;   // trace counters: triplets updated, rows executed, sub-phases with updates
   unsigned subbits;         //   sub-phases with updates (per-warp form)
 };
@@ -484,7 +502,7 @@ __device__ __forceinline__ int flow_subphases(const TiledArgs<T>& a, int w, Flow
         const uint32_t n1 = __ballot_sync(0xffffffffu, need ? nz(z1) : b1);
         const uint32_t n2 = __ballot_sync(0xffffffffu, need ? nz(z2) : b2);
         if (lane == 0) {
-          uint32_t* mw = a.mask + (int64_t)w * M::PER_BT;
+          uint32_t* mw = a.sparse ? sm.nmask : a.mask + (int64_t)w * M::PER_BT;
           if (n0 != m0) mw[q0] = n0;
           if (n1 != m1) mw[q1] = n1;
           if (n2 != m2) mw[q2] = n2;
@@ -661,8 +679,16 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
     gIK = reinterpret_cast<float*>(pIK);
     gJK = reinterpret_cast<float*>(pJK);
   }
-  T* zb = a.zt + (int64_t)w * (3 * B * C::BB);
-  const uint32_t* mb = a.mask + (int64_t)w * M::PER_BT;
+  T* zb = a.sparse ? a.sp_scratch + (int64_t)blockIdx.x * (3 * B * C::BB) : a.zt + (int64_t)w * (3 * B * C::BB);
+  const uint32_t* mb = a.sparse ? nullptr : a.mask + (int64_t)w * M::PER_BT;
+  int sp_n = 0;
+  long long sp_o = 0;
+  if (a.sparse) {   // the item's bits are rebuilt from its entries below
+    sp_n = a.sp_cnt[w];
+    sp_o = a.sp_off[w];
+    for (int e = tid; e < M::PER_BT; e += NTH) sm.mask[e] = 0u;
+    item_sync<WARP>();
+  }
 
   // round 1: x tiles and mask words (16-byte copies, L2 only)
   constexpr int XCH = C::BB * (int)sizeof(T) / 16;     // 16-byte chunks per tile
@@ -672,8 +698,20 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
     if (!ij) cp_async16(reinterpret_cast<char*>(sm.x[2]) + 16 * e, reinterpret_cast<const char*>(a.x + oJK) + 16 * e);
   }
   constexpr int MCH = M::PER_BT * 4 / 16;
-  for (int e = tid; e < MCH; e += NTH)
-    cp_async16(reinterpret_cast<char*>(sm.mask) + 16 * e, reinterpret_cast<const char*>(mb) + 16 * e);
+  if (!a.sparse) {
+    for (int e = tid; e < MCH; e += NTH)
+      cp_async16(reinterpret_cast<char*>(sm.mask) + 16 * e, reinterpret_cast<const char*>(mb) + 16 * e);
+  } else {
+    // entries: set the bit, place the value in the CTA's scratch block and,
+    // when they fit, in the staging array (ascending index = bit order)
+    for (int e = tid; e < sp_n; e += NTH) {
+      const uint32_t ix = a.sp_idx[sp_o + e];
+      const T v = a.sp_val[sp_o + e];
+      atomicOr(&sm.mask[ix >> 5], 1u << (ix & 31));
+      zb[ix] = v;
+      if (sp_n <= M::CAP) sm.dual[e] = v;
+    }
+  }
   for (int e = tid; e < B; e += NTH) sm.lcnt[e] = 0;
   if (tid == 0) {
     sm.dirty = 0;
@@ -721,7 +759,8 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
     if (q < M::PER_BT) {
       uint32_t bits = sm.mask[q];
       sm.pre[q] = run;
-      if (staged && bits) {
+      if (a.sparse) sm.nmask[q] = bits;
+      if (staged && bits && !a.sparse) {
         const int t = q / (3 * M::WPR), r = (q / M::WPR) % 3, wd = q % M::WPR;
         const T* src = zb + (int64_t)t * (3 * C::BB) + r * C::BB + wd * 32;
         int idx = run;
@@ -778,7 +817,7 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
   bool any_touched;
   if constexpr (WARP) any_touched = __any_sync(0xffffffffu, touched);
   else any_touched = __syncthreads_or(touched);
-  if (!WARP && SHADOW && sm.dirty) {
+  if (!WARP && SHADOW && sm.dirty && !a.sparse) {
     uint32_t* mw = a.mask + (int64_t)w * M::PER_BT;
     for (int e = tid; e < M::PER_BT; e += NTH) mw[e] = sm.mask[e];
   }
@@ -787,6 +826,62 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
       a.x[oIJ + e] = sm.x[0][e];
       if (!kj) a.x[oIK + e] = sm.x[1][e];
       if (!ij) a.x[oJK + e] = sm.x[2][e];
+    }
+  }
+  if (a.sparse) {
+    // the item's nonzero duals into the next pool, in bit (index) order;
+    // then the scratch block back to zero (every other slot already is)
+    int mine = 0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int q = tid * CH + c;
+      if (q < M::PER_BT) mine += __popc(sm.nmask[q]);
+    }
+    int inc = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    if (lane == 31) sm.scan[wid] = inc;
+    item_sync<WARP>();
+    if (wid == 0) {
+      int v = lane < NW ? sm.scan[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+      }
+      if (lane < NW) sm.scan[lane] = v;
+    }
+    item_sync<WARP>();
+    const int cnt_new = sm.scan[NW - 1];
+    if (tid == 0) {
+      sm.base = cnt_new ? atomicAdd(a.sp_top, (unsigned long long)cnt_new) : 0ull;
+      a.sp_cnt_next[w] = cnt_new;
+    }
+    item_sync<WARP>();
+    const unsigned long long base = sm.base;
+    const bool fits = base + (unsigned long long)cnt_new <= (unsigned long long)a.sp_cap;
+    if (tid == 0) a.sp_off_next[w] = fits ? (long long)base : -1ll;
+    long long pos = (long long)base + (wid ? sm.scan[wid - 1] : 0) + inc - mine;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int q = tid * CH + c;
+      if (q < M::PER_BT) {
+        uint32_t bits = sm.nmask[q];
+        while (bits) {
+          const int l = __ffs(bits) - 1;
+          bits &= bits - 1;
+          const uint32_t ix = (uint32_t)q * 32u + (uint32_t)l;
+          if (fits) {
+            a.sp_idx_next[pos] = ix;
+            a.sp_val_next[pos] = zb[ix];
+          }
+          ++pos;
+          zb[ix] = T(0);
+        }
+      }
     }
   }
   item_sync<WARP>();
@@ -1356,6 +1451,49 @@ template <typename S, typename D>
 __global__ void k_convert(const S* __restrict__ src, D* dst, int64_t count) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
     dst[e] = (D)src[e];
+}
+
+}  // namespace ccd
+
+namespace ccd {
+
+// Triangle duals of the sparse store in canonical order (caller labels):
+// every entry of every block triple is mapped to its triplet and row and,
+// when the triplet's rank lies in [first, first + count), written as
+// buf[3 (rank - first) + row] = scale * value.  buf must be zeroed first.
+// ilab maps internal to caller labels (nullptr: identity).  A row is named by
+// the object it leaves out: row 0 (hypotenuse ij) leaves out k, 1 leaves out
+// j, 2 leaves out i.
+template <int B>
+__global__ void k_tri_duals_sparse(const uint32_t* __restrict__ idx, const double* __restrict__ val,
+                                   const long long* __restrict__ off, const int* __restrict__ cnt,
+                                   const int* __restrict__ bt_list, int nbt, int n, const int* __restrict__ ilab,
+                                   int64_t first, int64_t count, double* buf, double scale) {
+  constexpr int BB = B * B;
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nbt; w += gridDim.x * blockDim.x) {
+    int I, J, K;
+    unpack_bt(bt_list[w], I, J, K);
+    const long long o = off[w];
+    const int m = cnt[w];
+    for (int e = 0; e < m; ++e) {
+      const uint32_t ix = idx[o + e];
+      const int t = (int)(ix / (3 * BB)), r = (int)((ix / BB) % 3), slot = (int)(ix % BB);
+      const int la = slot / B, lb = slot % B, lc = (t - la - lb) & (B - 1);
+      int a = I * B + la, b = J * B + lb, c = K * B + lc;       // internal labels, a < b < c
+      const int out = r == 0 ? c : (r == 1 ? b : a);
+      int co = out;
+      if (ilab) {
+        a = ilab[a];
+        b = ilab[b];
+        c = ilab[c];
+        co = ilab[out];
+      }
+      const int u = min(a, min(b, c)), z = max(a, max(b, c)), v = a + b + c - u - z;
+      const int row = co == z ? 0 : (co == v ? 1 : 2);
+      const int64_t rank = tri_rank(n, u, v, z);
+      if (rank >= first && rank < first + count) buf[3 * (rank - first) + row] = scale * val[o + e];
+    }
+  }
 }
 
 }  // namespace ccd

@@ -1,0 +1,145 @@
+"""The sparse dual store (store="sparse": per block triple a list of its
+nonzero duals, Sec. III-D) against the dense store on the GPU: the same
+sweeps in the same order with the same arithmetic, so x, f and all duals
+agree bit for bit, whatever the pool capacity (a sweep that overflows the
+next pool is undone and run again)."""
+import numpy as np
+import pytest
+
+from instances import chung_lu, noisy_euclidean, planted_partition, random_dissimilarity
+
+pytestmark = pytest.mark.gpu
+
+
+def _state(n, d, w, sweeps, **kw):
+    import paper_1901_10084_gb300 as cc
+    with cc.Solver(n, d, w, **kw) as s:
+        s.sweep(sweeps)
+        x, f = s.get_x()
+        yt, yp = s.get_duals()
+        st = s.stats()
+        nbytes = s.device_bytes()
+    return x, f, yt, yp, st, nbytes
+
+
+def _equal(a, b):
+    for u, v in zip(a[:4], b[:4]):
+        np.testing.assert_array_equal(u, v)
+
+
+CASES = [("cc", 60, 8, False, False), ("cc", 61, 16, True, True), ("cc", 150, 16, False, True),
+         ("cc", 97, 32, True, False), ("l2", 70, 16, True, True), ("l2", 90, 8, False, False)]
+
+
+def _inputs(problem, n, weighted):
+    if problem == "l2":
+        return random_dissimilarity(n, n, weights=(0.5, 2.0) if weighted else None)
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=n, weights=(0.5, 2.0) if weighted else None)
+    return d, w
+
+
+@pytest.mark.parametrize("variant", [0, 3, 4])
+@pytest.mark.parametrize("problem,n,tile,weighted,interleave", CASES)
+def test_sparse_store_equals_dense_bitwise(variant, problem, n, tile, weighted, interleave):
+    d, w = _inputs(problem, n, weighted)
+    kw = dict(tile=tile, interleave=interleave, problem=problem, variant=variant)
+    for sweeps in (1, 6):
+        dense = _state(n, d, w, sweeps, **kw)
+        sparse = _state(n, d, w, sweeps, store="sparse", **kw)
+        _equal(sparse, dense)
+        assert sparse[4]["dual_nnz"] == int(np.count_nonzero(dense[2]))
+        assert dense[4]["dual_nnz"] == -1
+
+
+@pytest.mark.parametrize("pool", [1, 64, 2000])
+def test_pool_overflow_undoes_and_reruns_the_sweep(pool):
+    n = 120
+    d, w, _ = planted_partition(n, 4, 0.6, 0.15, seed=3)
+    dense = _state(n, d, w, 8, tile=16)
+    sparse = _state(n, d, w, 8, tile=16, store="sparse", pool_entries=pool)
+    _equal(sparse, dense)
+    if pool < 2000:
+        assert sparse[4]["pool_retries"] > 0
+
+
+def test_sparse_solve_matches_dense():
+    import paper_1901_10084_gb300 as cc
+    n, d, w = 200, *chung_lu(200, 2.5, 8.0, seed=5)[:2]
+    out = []
+    for store in ("dense", "sparse"):
+        with cc.Solver(n, d, w, tile=16, store=store, check_every=5) as s:
+            conv, k = s.solve(1e-6, 20000)
+            st = s.check()
+            x, _ = s.get_x()
+        out.append((conv, k, st["lp_objective"], x))
+    assert out[0][0] and out[1][0] and out[0][1] == out[1][1]
+    assert out[0][2] == out[1][2] and np.array_equal(out[0][3], out[1][3])
+
+
+def test_sparse_dual_ranges():
+    import paper_1901_10084_gb300 as cc
+    n = 400
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=9)
+    T = n * (n - 1) * (n - 2) // 6
+    with cc.Solver(n, d, w, tile=16, store="sparse") as s:
+        s.sweep(4)
+        full, _ = s.get_duals()
+        for first, count in ((0, 1000), (T // 3, 5000), (T - 777, 777)):
+            part, _ = s.get_duals(first, count, pairs=False)
+            np.testing.assert_array_equal(part, full[3 * first: 3 * (first + count)])
+
+
+def test_sparse_store_memory():
+    """n = 800: the dense FP64 store and bitmask take 2.2 GB; the sparse store
+    (pools, tables, per-CTA scratch, snapshot) a small fraction of that."""
+    import paper_1901_10084_gb300 as cc
+    n = 800
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=9)
+    with cc.Solver(n, d, w, tile=16, store="sparse") as s, cc.Solver(n, d, w, tile=16) as t:
+        s.sweep(10)
+        t.sweep(10)
+        dense_bytes, sparse_bytes = t.device_bytes(), s.device_bytes()
+    assert dense_bytes > 2e9 and sparse_bytes < dense_bytes / 8
+
+
+def test_unsupported_combinations_are_refused():
+    import paper_1901_10084_gb300 as cc
+    from paper_1901_10084_gb300 import warmstart
+    n = 40
+    d, w, _ = planted_partition(n, 2, 0.7, 0.1, seed=1)
+    for kw in (dict(precision="fp32_refine"), dict(exact=True), dict(schedule="summod"),
+               dict(schedule="diagonal"), dict(variant=1), dict(variant=2)):
+        with pytest.raises(cc.CCError) as e:
+            cc.Solver(n, d, w, store="sparse", **kw)
+        assert e.value.code == cc.CC_ERR_UNSUPPORTED, kw
+    with cc.Solver(n, d, w, store="sparse", tile=8) as s:
+        s.sweep(2)
+        x, f = s.get_x()
+        yt, yp = s.get_duals()
+        for call in (lambda: s.set_state(x, f, yt, yp), lambda: s.set_duals(yt, yp),
+                     lambda: s.warm_start(warmstart.init_params(0))):
+            with pytest.raises(cc.CCError) as e:
+                call()
+            assert e.value.code == cc.CC_ERR_UNSUPPORTED
+    from paper_1901_10084_gb300 import _native
+    o = cc.cc_opts_default()
+    o.store = _native.CC_STORE_SPARSE
+    with pytest.raises(cc.CCError) as e:
+        _native.cc_batch_create([n], [d], [w], o)
+    assert e.value.code == cc.CC_ERR_UNSUPPORTED
+
+
+def test_large_instance_beyond_the_dense_store():
+    """n = 3000 (the dense FP64 store would need 108 GB): sweeps run, the
+    violation falls and the store holds only the nonzero duals."""
+    import paper_1901_10084_gb300 as cc
+    n = 3000
+    d, w = noisy_euclidean(n, 2, 0.2, 4)
+    with cc.Solver(n, d, w, problem="l2", tile=16, store="sparse") as s:
+        v0 = s.check()["max_violation"]
+        s.sweep(3)
+        st = s.check()
+        nbytes = s.device_bytes()
+    assert st["max_violation"] < v0
+    assert 0 < st["dual_nnz"] < 3 * n * (n - 1) * (n - 2) // 6 // 100
+    assert nbytes < 8e9
