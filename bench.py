@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--batch-count", type=int, default=256)
     p.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start measurement")
     p.add_argument("--no-l2", action="store_true", help="skip the l2 metric nearness measurement")
+    p.add_argument("--no-sparse", action="store_true", help="skip the sparse dual store measurement")
+    p.add_argument("--sparse-n", type=int, default=4000, help="size of the sparse-store solve")
     p.add_argument("--ws-train-count", type=int, default=2000,
                    help="Chung-Lu n=200 training instances for the warm-start network")
     p.add_argument("--ws-steps", type=int, default=3000)
@@ -255,6 +257,8 @@ def run_ours(args, rank, world, local_rank):
         out["warm_start"] = _warm_start(args, stream)
     if rank == 0 and not args.no_l2 and args.schedule == "tiled":
         out["l2_nearness"] = _l2(args, stream)
+    if rank == 0 and not args.no_sparse and args.schedule == "tiled":
+        out["sparse_store"] = _sparse(args, stream)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -394,6 +398,48 @@ def _l2(args, stream):
                      "time_to_tol": {"seconds": el, "sweeps": k, "converged": ok, "tol": args.tol,
                                      "max_violation": st["max_violation"], "objective": st["lp_objective"],
                                      "gap_rel": st["gap"] / st["qp_primal"] if st["qp_primal"] else 0.0}}
+    return rec
+
+
+def _sparse(args, stream):
+    """The sparse dual store: sweep time and device memory against the dense
+    store on the bench workload (after 60 sweeps), then a solve at a size the
+    dense store cannot hold (Chung-Lu, mean degree 8, seed 1)."""
+    import torch
+
+    import paper_1901_10084_gb300 as cc
+    from instances import chung_lu, workload
+    rec = {}
+    n, d, w, _ = workload(args.workload)
+    for store in ("dense", "sparse"):
+        with cc.Solver(n, d, w, tile=args.tile, store=store, stream=stream) as s:
+            s.sweep(60)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.sweep(20)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rec[f"{args.workload}_{store}"] = {"sweep_ms": e0.elapsed_time(e1) / 20,
+                                                "device_bytes": s.device_bytes(),
+                                                "dual_nnz": s.stats()["dual_nnz"]}
+    m = args.sparse_n
+    d, w, _ = chung_lu(m, 2.5, 8.0, seed=1)
+    with cc.Solver(m, d, w, tile=args.tile, store="sparse", check_every=args.check_every, stream=stream) as s:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ok, k = s.solve(args.tol, 1000)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t
+        st = s.check()
+        T = m * (m - 1) * (m - 2) // 6
+        rec[f"chunglu{m}_sparse"] = {
+            "time_to_tol": {"seconds": el, "sweeps": k, "converged": ok, "tol": args.tol,
+                            "max_violation": st["max_violation"], "lp_objective": st["lp_objective"]},
+            "last_sweep_ms": st["last_sweep_ms"], "triplets": T,
+            "device_bytes": s.device_bytes(), "dual_nnz": s.stats()["dual_nnz"],
+            "pool_retries": s.stats()["pool_retries"],
+            "dense_store_bytes": 3 * T * 8,
+            "desc": f"Chung-Lu n={m}, exponent 2.5, mean degree 8, seed 1, unit weights, FP64, sparse dual store"}
     return rec
 
 

@@ -147,8 +147,8 @@ typedef struct cc_opts {
                                warm start: CC_ERR_UNSUPPORTED); no batches.
                                Same values as the dense store. */
   int64_t pool_entries;     /* sparse store: initial capacity of each of the
-                               two entry pools (0 = max(2^20, 4 x block
-                               triples)).  A sweep whose next pool overflows
+                               two entry pools (0 = max(2^20, block
+                               triples / 2)).  A sweep whose next pool overflows
                                is undone and run again with the pool grown to
                                1.5 x the entries it needed. */
 } cc_opts;

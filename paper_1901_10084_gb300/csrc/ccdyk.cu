@@ -74,6 +74,7 @@ struct cc_handle {
   double* snap = nullptr;    // x, f, pair duals before a sparse sweep
   int64_t sp_nnz = 0;        // entries in the current pool
   int64_t sp_retries = 0;    // sweeps run again after the next pool grew
+  bool fresh = false;        // CC state still Algorithm 1's start (x = 0, all duals 0)
   std::vector<int> h_bt_off; // host copy of the phase offsets of the block triples
   // schedules 0 and 1 (device tables)
   ListArgs la{};
@@ -315,6 +316,22 @@ int configure_sweep(cc_handle* h) {
 
 int read_ctl_error(cc_handle* h);
 
+// Dataflow counters before a sweep.  From Algorithm 1's start of the CC
+// problem (x = 0, every dual 0) every metric row has delta = 0 and z = 0, so
+// its update is exactly a no-op (z' = max(0 + r * 0, 0) = 0, c = 0, x + 0 = x):
+// the first sweep then starts with every tile visited Nb times and the item
+// counter past the block triples, and only the pair items run.
+int reset_flow(cc_handle* h) {
+  if (h->fresh) {
+    k_fill<int><<<1, 1, 0, h->st>>>(h->flow, 1, h->nbt);
+    k_fill<int><<<grid_for(h, h->ntiles, 256), 256, 0, h->st>>>(h->flow + 1, h->ntiles, h->nb);
+    CK(h, cudaGetLastError());
+  } else {
+    CK(h, cudaMemsetAsync(h->flow, 0, (size_t)(1 + h->ntiles) * sizeof(int), h->st));
+  }
+  return CC_OK;
+}
+
 // One sweep with the sparse store: the current pool is only read, so a sweep
 // whose next pool overflows is undone (x, f and the pair duals back from the
 // snapshot), the next pool grows to the size the sweep reported, and the sweep
@@ -327,7 +344,8 @@ int sweep_sparse(cc_handle* h) {
     CK(h, cudaMemcpyAsync(h->snap + h->tile_elems, h->f, te, cudaMemcpyDeviceToDevice, h->st));
     CK(h, cudaMemcpyAsync(h->snap + 2 * h->tile_elems, h->zp, 2 * te, cudaMemcpyDeviceToDevice, h->st));
     CK(h, cudaMemsetAsync(h->sp_top, 0, sizeof(unsigned long long), h->st));
-    CK(h, cudaMemsetAsync(h->flow, 0, (size_t)(1 + h->ntiles) * sizeof(int), h->st));
+    int rc0 = reset_flow(h);
+    if (rc0) return rc0;
     int* flow = h->flow;
     TiledArgs<double> a = tiled_args<double>(h);
     void* args[] = {&a, &flow};
@@ -383,7 +401,8 @@ int launch_sweep(cc_handle* h) {
     return CC_OK;
   }
   if (h->sparse) return sweep_sparse(h);
-  CK(h, cudaMemsetAsync(h->flow, 0, (size_t)(1 + h->ntiles) * sizeof(int), h->st));
+  int rc0 = reset_flow(h);
+  if (rc0) return rc0;
   int* flow = h->flow;
   if (h->fp32) {
     TiledArgs<float> a = tiled_args<float>(h);
@@ -589,7 +608,7 @@ int init_state(cc_handle* h) {
 // Sparse store: two pools (entries), their tables, the per-CTA scratch
 // blocks (zero), the snapshot for undoing a sweep, and the inverse labels.
 int alloc_sparse(cc_handle* h) {
-  const int64_t cap = h->o.pool_entries > 0 ? h->o.pool_entries : std::max<int64_t>((int64_t)1 << 20, 4 * (int64_t)h->nbt);
+  const int64_t cap = h->o.pool_entries > 0 ? h->o.pool_entries : std::max<int64_t>((int64_t)1 << 20, (int64_t)h->nbt / 2);
   for (int p = 0; p < 2; ++p) {
     h->sp_idx[p] = (uint32_t*)dalloc(h, (size_t)cap * sizeof(uint32_t));
     h->sp_val[p] = (double*)dalloc(h, (size_t)cap * sizeof(double));
@@ -702,6 +721,8 @@ int create_common(cc_handle** out, int64_t n, const double* d_dev, const double*
     rc = init_state<double>(h);
   }
   if (rc) return rc;
+  // (not while the fault-injection hook is armed: it acts on block triples)
+  h->fresh = h->o.problem == CC_PROB_CC && h->o.schedule == CC_SCHED_TILED && !h->o.exact && h->o.debug_skip_cta < 0;
   CK(h, cudaEventCreate(&h->ev0));
   CK(h, cudaEventCreate(&h->ev1));
   rc = configure_sweep(h);
@@ -915,11 +936,13 @@ int cc_sweep(cc_handle* h, int64_t k) {
     if (last) CK(h, cudaEventRecord(h->ev0, h->st));
     int rc = launch_sweep(h);
     if (rc) return rc;
+    h->fresh = false;
     if (last) {
       CK(h, cudaEventRecord(h->ev1, h->st));
       h->ev_recorded = true;
     }
     h->sweeps++;
+    h->fresh = false;
     if (h->fp32) h->fp32_sweeps++;
   }
   return CC_OK;
@@ -1193,6 +1216,7 @@ int cc_set_state(cc_handle* h, const double* x, const double* f, const double* y
     CK(h, cudaStreamSynchronize(h->st));
   }
   h->sweeps = 0;
+  h->fresh = false;
   return CC_OK;
 }
 
@@ -1221,6 +1245,7 @@ int cc_set_duals(cc_handle* h, const double* y_tri, const double* y_pair) {
   rc = resync_fp64(h);
   if (rc) return rc;
   h->sweeps = 0;
+  h->fresh = false;
   h->fp32_sweeps = 0;
   return CC_OK;
 }
@@ -1410,6 +1435,7 @@ int batch_launch(cc_batch* b, int gi) {
     cc_handle* h = b->hs[i];
     if (!b->active[i] || h->fp32 != (gi == 1)) continue;
     h->sweeps++;
+    h->fresh = false;
     if (h->fp32) h->fp32_sweeps++;
   }
   return CC_OK;
@@ -1734,6 +1760,7 @@ int cc_warm_start_mlp(cc_handle* h, const float* params, double threshold, int64
   ws_release(h, c);
   if (rc) return rc;
   h->sweeps = 0;
+  h->fresh = false;
   h->fp32_sweeps = 0;
   if (candidates) *candidates = c.count;
   return CC_OK;

@@ -75,3 +75,35 @@ def test_filtered_forms_equal_the_unfiltered_sweep(n, tile, weighted, interleave
         got = _run(n, d, w, 20, variant=2, **kw)
         for u, r in zip(got[:4], ref[:4]):
             assert np.array_equal(u, r)
+
+
+@pytest.mark.parametrize("store", ["dense", "sparse"])
+@pytest.mark.parametrize("n,tile,weighted", [(60, 8, False), (130, 16, True), (97, 32, False)])
+def test_first_sweep_shortcut_is_exact(store, n, tile, weighted):
+    """From Algorithm 1's start every metric row is a no-op, so the first
+    sweep runs only the pair rows; it must equal a full first sweep (forced
+    by setting the same start state, which turns the shortcut off) bit for
+    bit, and the oracle's first sweep to 1e-12 (the fused rounding)."""
+    import oracle
+    import paper_1901_10084_gb300 as cc
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=n, weights=(0.5, 2.0) if weighted else None)
+    P = len(d)
+    T = n * (n - 1) * (n - 2) // 6
+    o = oracle.State(n, d, w, 0.2)
+    x0, f0 = o.x.copy(), o.f.copy()
+    o.sweep(2, tile)
+    kw = dict(tile=tile, interleave=False)
+    a = _run(n, d, w, 1, **kw)
+    with cc.Solver(n, d, w, **kw) as s:
+        s.set_state(x0, f0, np.zeros(3 * T), np.zeros(2 * P))
+        s.sweep(1)
+        x, f = s.get_x()
+        yt, yp = s.get_duals()
+    for u, v in zip(a[:4], (x, f, yt, yp)):
+        assert np.array_equal(u, v)
+    assert np.max(np.abs(a[0] - o.x)) <= 1e-12 and np.max(np.abs(a[1] - o.f)) <= 1e-12
+    if store == "sparse":
+        b = _run(n, d, w, 3, store="sparse", **kw)
+        c = _run(n, d, w, 3, **kw)
+        for u, v in zip(b[:4], c[:4]):
+            assert np.array_equal(u, v)
