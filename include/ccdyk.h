@@ -47,6 +47,9 @@ extern "C" {
 #define CC_ERR_TIMEOUT 4       /* a grid barrier inside a sweep hit its time limit */
 #define CC_ERR_NOT_CONVERGED 5 /* cc_solve reached max_sweeps */
 #define CC_ERR_UNSUPPORTED 6   /* valid request this build does not serve */
+#define CC_ERR_BOUNDS 7        /* checked build (libccdyk_checked.so, compiled with CCD_CHECKED): a
+                                  sweep computed an offset outside its buffers; the access was
+                                  skipped and the state is undefined */
 
 /* Dual stores (opts.store). */
 #define CC_STORE_DENSE 0

@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _native
 from ._native import (CCError, CC_OK, CC_ERR_ARG, CC_ERR_OOM, CC_ERR_CUDA, CC_ERR_TIMEOUT,
-                      CC_ERR_NOT_CONVERGED, CC_ERR_UNSUPPORTED, CC_SCHED_DIAGONAL,
+                      CC_ERR_NOT_CONVERGED, CC_ERR_UNSUPPORTED, CC_ERR_BOUNDS, CC_SCHED_DIAGONAL,
                       CC_SCHED_SUMMOD, CC_SCHED_TILED, CC_PREC_FP64, CC_PREC_FP32_REFINE,
                       cc_opts_default, cc_create, cc_create_device, cc_sweep, cc_check, cc_solve,
                       cc_get_x, cc_get_duals, cc_set_state, cc_get_stats, cc_device_bytes,

@@ -19,6 +19,7 @@ CC_ERR_CUDA = 3
 CC_ERR_TIMEOUT = 4
 CC_ERR_NOT_CONVERGED = 5
 CC_ERR_UNSUPPORTED = 6
+CC_ERR_BOUNDS = 7
 
 CC_SCHED_DIAGONAL = 0
 CC_SCHED_SUMMOD = 1
@@ -101,7 +102,8 @@ _lock = threading.Lock()
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """libccdyk.so, or libccdyk_checked.so when CCDYK_CHECKED=1."""
+    return _build.LIB_CHECKED if os.environ.get("CCDYK_CHECKED") == "1" else _build.LIB
 
 
 def load(build_if_missing: bool = False) -> ctypes.CDLL:
@@ -112,11 +114,12 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
             return _lib
         if build_if_missing:
             _build.build()
-        if not os.path.exists(_build.LIB):
+        path = lib_path()
+        if not os.path.exists(path):
             raise RuntimeError(
-                f"libccdyk.so not built at {_build.LIB}; run __graft_entry__.build() "
+                f"{os.path.basename(path)} not built at {path}; run __graft_entry__.build() "
                 "(the CUDA library is the only implementation)")
-        lib = ctypes.CDLL(_build.LIB)
+        lib = ctypes.CDLL(path)
         H = ctypes.c_void_p
         HP = ctypes.POINTER(ctypes.c_void_p)
         i64, dp = ctypes.c_int64, ctypes.POINTER(ctypes.c_double)

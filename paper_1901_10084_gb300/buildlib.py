@@ -1,4 +1,7 @@
-"""Build the CUDA library libccdyk.so in-tree for sm_103a (nvcc, no cmake)."""
+"""Build the CUDA library libccdyk.so in-tree for sm_103a (nvcc, no cmake), and
+its checked variant libccdyk_checked.so (CCD_CHECKED: the sweep kernels test
+their offsets and report CC_ERR_BOUNDS instead of touching memory outside their
+buffers).  Both compile in parallel."""
 from __future__ import annotations
 
 import os
@@ -11,6 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libccdyk.so")
+LIB_CHECKED = os.path.join(LIBDIR, "libccdyk_checked.so")
 SOURCES = [os.path.join(CSRC, "ccdyk.cu"), os.path.join(CSRC, "noalloc.cu")]
 DEPENDS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")] + [
     os.path.join(INCLUDE, "ccdyk.h")]
@@ -27,23 +31,29 @@ def nvcc() -> str:
     return "nvcc"
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(s) <= t for s in DEPENDS)
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
+    """Build both libraries (only those out of date); returns the normal one."""
     os.makedirs(LIBDIR, exist_ok=True)
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), *NVCC_FLAGS, "-I" + INCLUDE, "-I" + CSRC, "-o", tmp, *SOURCES]
-    if verbose:
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    jobs = []
+    for lib, extra in ((LIB, []), (LIB_CHECKED, ["-DCCD_CHECKED"])):
+        if not force and up_to_date(lib):
+            continue
+        tmp = lib + f".{os.getpid()}.tmp"
+        cmd = [nvcc(), *NVCC_FLAGS, *extra, "-I" + INCLUDE, "-I" + CSRC, "-o", tmp, *SOURCES]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        jobs.append((subprocess.Popen(cmd), tmp, lib, cmd))
+    for proc, tmp, lib, cmd in jobs:
+        if proc.wait() != 0:
+            raise subprocess.CalledProcessError(proc.returncode, cmd)
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -254,6 +254,10 @@ TiledArgs<T> tiled_args(cc_handle* h) {
   a.compact = h->o.variant == 1 ? 1 : 0;
   a.nofilter = h->o.variant == 4 ? 1 : 0;
   a.sparse = h->sparse ? 1 : 0;
+  a.zt_elems = (long long)h->zt_elems;
+  a.mask_words = (long long)h->mask_words;
+  a.sp_cap_cur = h->sparse ? (long long)h->sp_cap[h->sp_cur] : 0;
+  a.scratch_ctas = h->sparse ? (long long)h->sweep_grid : 0;
   if (h->sparse) {
     const int c = h->sp_cur, nx = 1 - c;
     a.sp_idx = h->sp_idx[c];
@@ -581,8 +585,11 @@ int read_ctl_error(cc_handle* h) {
     CK(h, cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), h->st));
     CK(h, cudaStreamSynchronize(h->st));
     char buf[160];
-    snprintf(buf, sizeof buf, "grid barrier time limit hit in phase %d of a sweep; the state is undefined",
-             c.err_phase);
+    if (c.err == CC_ERR_BOUNDS)
+      snprintf(buf, sizeof buf, "an offset outside its buffer was caught by the checked build; the state is undefined");
+    else
+      snprintf(buf, sizeof buf, "grid barrier time limit hit in phase %d of a sweep; the state is undefined",
+               c.err_phase);
     return fail(h, c.err, buf);
   }
   return CC_OK;

@@ -183,6 +183,19 @@ struct Ctl {            // device control block (scratch)
   int pad;
 };
 
+// Checked build (CCD_CHECKED): CCD_IN_BOUNDS(cond, ctl) records CC_ERR_BOUNDS
+// in the control block when cond is false and returns cond, so the caller
+// skips the access; in the normal build it is `true` and compiles away.
+#ifdef CCD_CHECKED
+__device__ __forceinline__ bool ccd_in_bounds(bool ok, Ctl* ctl) {
+  if (!ok) atomicCAS(&ctl->err, 0, CC_ERR_BOUNDS);
+  return ok;
+}
+#define CCD_IN_BOUNDS(cond, ctl) ccd_in_bounds((cond), (ctl))
+#else
+#define CCD_IN_BOUNDS(cond, ctl) true
+#endif
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -71,6 +71,8 @@ struct TiledArgs {
   unsigned long long* sp_top;
   long long sp_cap;     // entries the next pool holds
   T* sp_scratch;        // 3 B^3 values per CTA, all zero between items
+  // buffer sizes, for the checked build's offset tests
+  long long zt_elems, mask_words, sp_cap_cur, scratch_ctas;
 };
 
 __device__ __forceinline__ void unpack_bt(int pk, int& I, int& J, int& K) {
@@ -681,6 +683,20 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
   }
   T* zb = a.sparse ? a.sp_scratch + (int64_t)blockIdx.x * (3 * B * C::BB) : a.zt + (int64_t)w * (3 * B * C::BB);
   const uint32_t* mb = a.sparse ? nullptr : a.mask + (int64_t)w * M::PER_BT;
+  {
+    // checked build: every offset this item uses, tested once (the same
+    // result in every thread, so the item is skipped as a whole)
+    const long long te = (long long)a.ntiles * C::BB;
+    bool ok = w >= 0 && w < a.nbt && oIJ >= 0 && oIJ + C::BB <= te && oIK >= 0 && oIK + C::BB <= te &&
+              oJK >= 0 && oJK + C::BB <= te;
+    if (a.sparse) {
+      ok = ok && (long long)blockIdx.x < a.scratch_ctas && a.sp_off[w] >= 0 && a.sp_cnt[w] >= 0 &&
+           a.sp_off[w] + a.sp_cnt[w] <= a.sp_cap_cur;
+    } else {
+      ok = ok && ((long long)w + 1) * (3 * B * C::BB) <= a.zt_elems && ((long long)w + 1) * M::PER_BT <= a.mask_words;
+    }
+    if (!CCD_IN_BOUNDS(ok, a.ctl)) return;
+  }
   int sp_n = 0;
   long long sp_o = 0;
   if (a.sparse) {   // the item's bits are rebuilt from its entries below
@@ -707,6 +723,7 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
     for (int e = tid; e < sp_n; e += NTH) {
       const uint32_t ix = a.sp_idx[sp_o + e];
       const T v = a.sp_val[sp_o + e];
+      if (!CCD_IN_BOUNDS(ix < (uint32_t)(3 * B * C::BB), a.ctl)) continue;
       atomicOr(&sm.mask[ix >> 5], 1u << (ix & 31));
       zb[ix] = v;
       if (sp_n <= M::CAP) sm.dual[e] = v;

@@ -96,3 +96,13 @@ def test_warm_start_parameter_count_matches_the_network():
     assert p.shape == (N.CC_WS_NPARAM,) and p.dtype.name == "float32"
     W1, b1, W2, b2, W3, b3 = warmstart.unpack(p)
     assert W1.shape == (5, 64) and W2.shape == (64, 64) and W3.shape == (64, 3) and b3.shape == (3,)
+
+
+def test_checked_library_exports_the_same_symbols(lib):
+    """libccdyk_checked.so (CCD_CHECKED) is built beside the normal library."""
+    from paper_1901_10084_gb300 import buildlib
+    chk = ctypes.CDLL(buildlib.LIB_CHECKED)
+    for name in _declared():
+        assert hasattr(chk, name), name
+    src = open(os.path.join(ROOT, "include", "ccdyk.h")).read()
+    assert re.search(r"#define CC_ERR_BOUNDS 7\b", src)
