@@ -59,6 +59,9 @@ def parse():
     p.add_argument("--no-l2", action="store_true", help="skip the l2 metric nearness measurement")
     p.add_argument("--no-sparse", action="store_true", help="skip the sparse dual store measurement")
     p.add_argument("--sparse-n", type=int, default=4000, help="size of the sparse-store solve")
+    p.add_argument("--sparse-tile", type=int, default=16,
+                   help="tile of the sparse-store solve (32 above n = 16368: at most 1023 blocks)")
+    p.add_argument("--sparse-max-sweeps", type=int, default=1000)
     p.add_argument("--ws-train-count", type=int, default=2000,
                    help="Chung-Lu n=200 training instances for the warm-start network")
     p.add_argument("--ws-steps", type=int, default=3000)
@@ -424,10 +427,11 @@ def _sparse(args, stream):
                                                 "dual_nnz": s.stats()["dual_nnz"]}
     m = args.sparse_n
     d, w, _ = chung_lu(m, 2.5, 8.0, seed=1)
-    with cc.Solver(m, d, w, tile=args.tile, store="sparse", check_every=args.check_every, stream=stream) as s:
+    with cc.Solver(m, d, w, tile=args.sparse_tile, store="sparse", check_every=args.check_every,
+                   stream=stream) as s:
         torch.cuda.synchronize()
         t = time.perf_counter()
-        ok, k = s.solve(args.tol, 1000)
+        ok, k = s.solve(args.tol, args.sparse_max_sweeps)
         torch.cuda.synchronize()
         el = time.perf_counter() - t
         st = s.check()
@@ -439,7 +443,8 @@ def _sparse(args, stream):
             "device_bytes": s.device_bytes(), "dual_nnz": s.stats()["dual_nnz"],
             "pool_retries": s.stats()["pool_retries"],
             "dense_store_bytes": 3 * T * 8,
-            "desc": f"Chung-Lu n={m}, exponent 2.5, mean degree 8, seed 1, unit weights, FP64, sparse dual store"}
+            "desc": f"Chung-Lu n={m}, exponent 2.5, mean degree 8, seed 1, unit weights, FP64, sparse dual store, "
+                    f"tile {args.sparse_tile}"}
     return rec
 
 
