@@ -51,7 +51,7 @@ struct cc_handle {
   int64_t tile_elems = 0;   // ntiles * B * B
   int64_t zt_elems = 0;     // nbt * 3 * B^3
   // schedule tables
-  int* bt_list = nullptr;
+  btpk* bt_list = nullptr;
   int* bt_off = nullptr;
   int* tile_list = nullptr;
   int* bt_rank = nullptr;
@@ -424,7 +424,10 @@ int launch_sweep(cc_handle* h) {
 
 int build_tables(cc_handle* h) {
   const int nb = h->nb, B = h->B;
-  std::vector<int> list, off(nb + 1, 0), rank((size_t)nb * nb * nb, -1), tiles;
+  // the rank table (O(nb^3)) serves the dense store only
+  const bool dense = h->o.store == CC_STORE_DENSE;
+  std::vector<btpk> list;
+  std::vector<int> off(nb + 1, 0), rank(dense ? (size_t)nb * nb * nb : 1, -1), tiles;
   // triplets in block triple (I,J,K): products of block sizes, with
   // binomials where blocks coincide
   auto bsize = [&](int I) { return (int64_t)std::min<int64_t>(B, h->n - (int64_t)I * B); };
@@ -434,7 +437,7 @@ int build_tables(cc_handle* h) {
     if (J == K) return bsize(I) * ch2(bsize(J));
     return bsize(I) * bsize(J) * bsize(K);
   };
-  std::vector<std::pair<int64_t, int>> ph;
+  std::vector<std::pair<int64_t, btpk>> ph;
   for (int g = 0; g < nb; ++g) {
     off[g] = (int)list.size();
     ph.clear();
@@ -442,15 +445,16 @@ int build_tables(cc_handle* h) {
       for (int J = I; J < nb; ++J) {
         int K = ((g - I - J) % nb + 2 * nb) % nb;
         if (K < J) continue;
-        ph.push_back({-count(I, J, K), I | (J << 10) | (K << 20)});
+        ph.push_back({-count(I, J, K), pack_bt(I, J, K)});
       }
     // largest first, so that the dynamic distribution ends the phase with
     // the smallest items
     std::stable_sort(ph.begin(), ph.end(),
-                     [](const std::pair<int64_t, int>& x, const std::pair<int64_t, int>& y) { return x.first < y.first; });
+                     [](const std::pair<int64_t, btpk>& x, const std::pair<int64_t, btpk>& y) { return x.first < y.first; });
     for (auto& e : ph) {
-      const int I = e.second & 1023, J = (e.second >> 10) & 1023, K = (e.second >> 20) & 1023;
-      rank[((size_t)I * nb + J) * nb + K] = (int)list.size();
+      int I, J, K;
+      unpack_bt(e.second, I, J, K);
+      if (dense) rank[((size_t)I * nb + J) * nb + K] = (int)list.size();
       list.push_back(e.second);
     }
     h->max_bt_phase = std::max(h->max_bt_phase, (int)list.size() - off[g]);
@@ -463,12 +467,12 @@ int build_tables(cc_handle* h) {
   h->ntiles = (int)tiles.size();
   h->tile_elems = (int64_t)h->ntiles * B * B;
   h->zt_elems = (int64_t)h->nbt * 3 * B * B * B;
-  h->bt_list = (int*)dalloc(h, list.size() * sizeof(int));
+  h->bt_list = (btpk*)dalloc(h, list.size() * sizeof(btpk));
   h->bt_off = (int*)dalloc(h, off.size() * sizeof(int));
   h->bt_rank = (int*)dalloc(h, rank.size() * sizeof(int));
   h->tile_list = (int*)dalloc(h, tiles.size() * sizeof(int));
   if (!h->bt_list || !h->bt_off || !h->bt_rank || !h->tile_list) return fail(h, CC_ERR_OOM, "schedule tables");
-  CK(h, cudaMemcpyAsync(h->bt_list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CK(h, cudaMemcpyAsync(h->bt_list, list.data(), list.size() * sizeof(btpk), cudaMemcpyHostToDevice, h->st));
   CK(h, cudaMemcpyAsync(h->bt_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
   CK(h, cudaMemcpyAsync(h->bt_rank, rank.data(), rank.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
   CK(h, cudaMemcpyAsync(h->tile_list, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice, h->st));
@@ -654,7 +658,9 @@ int create_common(cc_handle** out, int64_t n, const double* d_dev, const double*
   h->T3 = ch3(n);
   h->B = h->o.tile;
   h->nb = (int)((n + h->B - 1) / h->B);
-  if (h->nb > 1023) return fail(h, CC_ERR_ARG, "n / tile exceeds 1023 blocks");
+  // the rank table of the dense store has nb^3 entries; the sparse store has none
+  if (h->o.store == CC_STORE_DENSE && h->nb > 1023) return fail(h, CC_ERR_ARG, "n / tile exceeds 1023 blocks");
+  if (h->nb > 2047) return fail(h, CC_ERR_ARG, "n / tile exceeds 2047 blocks");
   (void)opts;
   // validate inputs on device
   int* flags = (int*)dalloc(h, 4 * sizeof(int));
@@ -807,7 +813,7 @@ int resync_fp64(cc_handle* h) {
   const uint32_t* mask = h->mask;
   int nb = h->nb;
   int n = (int)h->n;
-  const int* bl = h->bt_list;
+  const btpk* bl = h->bt_list;
   const int* bo = h->bt_off;
   Ctl* ctl = h->ctl;
   long long tns = (long long)(h->o.barrier_timeout_s * 1e9);

@@ -183,6 +183,13 @@ struct Ctl {            // device control block (scratch)
   int pad;
 };
 
+// A block triple I <= J <= K of the tiled schedule, packed in 64 bits (21 bits
+// per block index).
+typedef unsigned long long btpk;
+__host__ __device__ __forceinline__ btpk pack_bt(int I, int J, int K) {
+  return (btpk)I | ((btpk)J << 21) | ((btpk)K << 42);
+}
+
 // Checked build (CCD_CHECKED): CCD_IN_BOUNDS(cond, ctl) records CC_ERR_BOUNDS
 // in the control block when cond is false and returns cond, so the caller
 // skips the access; in the normal build it is `true` and compiles away.

@@ -39,7 +39,7 @@ struct TiledArgs {
   const T* winv;        // tile-major 1/w
   T* zt;                // triangle duals, 3 B^3 per block triple
   T* zp;                // pair duals, 2 B^2 per tile (row +, row -)
-  const int* bt_list;   // block triples in schedule order, packed I | J<<10 | K<<20
+  const btpk* bt_list;  // block triples in schedule order, packed by pack_bt
   const int* bt_off;    // nb+1 offsets of the phases in bt_list
   const int* tile_list; // tiles in tile_index order, packed I | J<<16
   Ctl* ctl;
@@ -75,10 +75,10 @@ struct TiledArgs {
   long long zt_elems, mask_words, sp_cap_cur, scratch_ctas;
 };
 
-__device__ __forceinline__ void unpack_bt(int pk, int& I, int& J, int& K) {
-  I = pk & 1023;
-  J = (pk >> 10) & 1023;
-  K = (pk >> 20) & 1023;
+__host__ __device__ __forceinline__ void unpack_bt(btpk pk, int& I, int& J, int& K) {
+  I = (int)(pk & 0x1fffffull);
+  J = (int)((pk >> 21) & 0x1fffffull);
+  K = (int)(pk >> 42);
 }
 
 // Project every triplet of block triple number w (schedule rank).
@@ -1128,7 +1128,7 @@ struct SumOp {
 // The maximum is order-free, so the result equals a serial FP64 evaluation.
 template <typename T, int B>
 __global__ void __launch_bounds__(TileCfg<B>::NT) k_maxviol_tiled(const T* __restrict__ x, int n, int nb,
-                                                                   const int* __restrict__ bt_list, int nbt,
+                                                                   const btpk* __restrict__ bt_list, int nbt,
                                                                    double* part) {
   using C = TileCfg<B>;
   __shared__ T sx[3][C::BB];
@@ -1387,7 +1387,7 @@ __global__ void k_pair_duals_tiled(T* zp, int n, int nb, int B, double* buf, dou
 template <int B>
 __global__ void __launch_bounds__(TileCfg<B>::NT) k_resync_metric(const double* __restrict__ zt,
                                                                    const uint32_t* __restrict__ mask, double* acc,
-                                                                   int n, int nb, const int* __restrict__ bt_list,
+                                                                   int n, int nb, const btpk* __restrict__ bt_list,
                                                                    const int* __restrict__ bt_off, Ctl* ctl,
                                                                    long long timeout_ns) {
   using C = TileCfg<B>;
@@ -1484,7 +1484,7 @@ namespace ccd {
 template <int B>
 __global__ void k_tri_duals_sparse(const uint32_t* __restrict__ idx, const double* __restrict__ val,
                                    const long long* __restrict__ off, const int* __restrict__ cnt,
-                                   const int* __restrict__ bt_list, int nbt, int n, const int* __restrict__ ilab,
+                                   const btpk* __restrict__ bt_list, int nbt, int n, const int* __restrict__ ilab,
                                    int64_t first, int64_t count, double* buf, double scale) {
   constexpr int BB = B * B;
   for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nbt; w += gridDim.x * blockDim.x) {
