@@ -171,3 +171,18 @@ def test_unsupported_combinations_are_refused():
         with pytest.raises(cc.CCError) as e:
             s.warm_start(warmstart.init_params(0))
         assert e.value.code == cc.CC_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("exact", [True, False])
+def test_worked_triangle_case_on_gpu(exact):
+    """Sec. II-B's worked projection (tests/golden/worked_triangle.json) as an
+    l2 sweep of n = 3 through the C ABI."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "worked_triangle.json")))
+    for case in g["cases"]:
+        d = np.array(case["x_before"])
+        with _solver(3, d, np.ones(3), tile=8, exact=exact) as s:
+            s.sweep(1)
+            x, _ = s.get_x()
+        np.testing.assert_allclose(x, case["x_after"], rtol=0, atol=4e-16)

@@ -115,3 +115,21 @@ def test_schedules_reach_the_same_optimum():
         xs.append(s.x.copy())
     np.testing.assert_allclose(xs[0], xs[1], atol=1e-9)
     np.testing.assert_allclose(xs[0], xs[2], atol=1e-9)
+
+
+def test_worked_triangle_case_is_the_l2_solution():
+    """The paper's worked projection (Sec. II-B, W = I, tests/golden/
+    worked_triangle.json) is an l2 metric nearness step: starting from
+    x = d = x_before, one l2 sweep of n = 3 gives x_after, which is then the
+    optimum (one halfspace active)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "worked_triangle.json")))
+    for case in g["cases"]:
+        d = np.array(case["x_before"])
+        for sched in (0, 1, 2):
+            s = oracle.State(3, d, np.ones(3), problem="l2")
+            s.sweep(sched, 2)
+            np.testing.assert_allclose(s.x, case["x_after"], rtol=0, atol=2e-16)
+            s.sweep(sched, 2)
+            np.testing.assert_allclose(s.x, case["x_after"], rtol=0, atol=2e-16)
