@@ -144,8 +144,9 @@ typedef struct cc_opts {
                                block triple a list of its nonzero duals
                                (local index, value) in visiting order, so
                                memory is O(n^2 + nonzero duals).  Needs the
-                               tiled schedule, fused form, FP64 and variant
-                               0, 3 or 4; duals can be read (cc_get_duals)
+                               tiled schedule, fused form and variant 0, 3
+                               or 4 (FP64 or the FP32 bulk form); duals can
+                               be read (cc_get_duals)
                                but not set (cc_set_state, cc_set_duals,
                                warm start: CC_ERR_UNSUPPORTED); no batches.
                                Same values as the dense store. */

@@ -64,13 +64,14 @@ struct cc_handle {
   // sparse dual store (opts.store = CC_STORE_SPARSE): two pools of entries
   bool sparse = false;
   uint32_t* sp_idx[2] = {nullptr, nullptr};
-  double* sp_val[2] = {nullptr, nullptr};
+  void* sp_val[2] = {nullptr, nullptr};      // values in the state's type (float in the FP32 phase)
   long long* sp_off[2] = {nullptr, nullptr};
   int* sp_cnt[2] = {nullptr, nullptr};
   int64_t sp_cap[2] = {0, 0};
   int sp_cur = 0;            // pool read by the next sweep
   unsigned long long* sp_top = nullptr;
   double* sp_scratch = nullptr;   // 3 B^3 doubles per CTA of the sweep
+  int sp_scratch_ctas = 0;        // CTAs the scratch holds blocks for
   double* snap = nullptr;    // x, f, pair duals before a sparse sweep
   int64_t sp_nnz = 0;        // entries in the current pool
   int64_t sp_retries = 0;    // sweeps run again after the next pool grew
@@ -257,7 +258,7 @@ TiledArgs<T> tiled_args(cc_handle* h) {
   a.zt_elems = (long long)h->zt_elems;
   a.mask_words = (long long)h->mask_words;
   a.sp_cap_cur = h->sparse ? (long long)h->sp_cap[h->sp_cur] : 0;
-  a.scratch_ctas = h->sparse ? (long long)h->sweep_grid : 0;
+  a.scratch_ctas = h->sparse ? (long long)h->sp_scratch_ctas : 0;
   if (h->sparse) {
     const int c = h->sp_cur, nx = 1 - c;
     a.sp_idx = h->sp_idx[c];
@@ -340,18 +341,20 @@ int reset_flow(cc_handle* h) {
 // whose next pool overflows is undone (x, f and the pair duals back from the
 // snapshot), the next pool grows to the size the sweep reported, and the sweep
 // runs again.  Synchronizes once per sweep.
-int sweep_sparse(cc_handle* h) {
-  const size_t te = (size_t)h->tile_elems * sizeof(double);
+template <typename T>
+int sweep_sparse_t(cc_handle* h) {
+  const size_t te = (size_t)h->tile_elems * sizeof(T);
+  char* snap = (char*)h->snap;
   void* k = sweep_kernel(h);
   for (int attempt = 0; attempt < 4; ++attempt) {
-    CK(h, cudaMemcpyAsync(h->snap, h->x, te, cudaMemcpyDeviceToDevice, h->st));
-    CK(h, cudaMemcpyAsync(h->snap + h->tile_elems, h->f, te, cudaMemcpyDeviceToDevice, h->st));
-    CK(h, cudaMemcpyAsync(h->snap + 2 * h->tile_elems, h->zp, 2 * te, cudaMemcpyDeviceToDevice, h->st));
+    CK(h, cudaMemcpyAsync(snap, h->x, te, cudaMemcpyDeviceToDevice, h->st));
+    CK(h, cudaMemcpyAsync(snap + te, h->f, te, cudaMemcpyDeviceToDevice, h->st));
+    CK(h, cudaMemcpyAsync(snap + 2 * te, h->zp, 2 * te, cudaMemcpyDeviceToDevice, h->st));
     CK(h, cudaMemsetAsync(h->sp_top, 0, sizeof(unsigned long long), h->st));
     int rc0 = reset_flow(h);
     if (rc0) return rc0;
     int* flow = h->flow;
-    TiledArgs<double> a = tiled_args<double>(h);
+    TiledArgs<T> a = tiled_args<T>(h);
     void* args[] = {&a, &flow};
     CK(h, cudaLaunchCooperativeKernel(k, h->sweep_grid, h->sweep_threads, args, h->dyn_smem, h->st));
     unsigned long long top = 0;
@@ -365,21 +368,23 @@ int sweep_sparse(cc_handle* h) {
     }
     int rc = read_ctl_error(h);
     if (rc) return rc;
-    CK(h, cudaMemcpyAsync(h->x, h->snap, te, cudaMemcpyDeviceToDevice, h->st));
-    CK(h, cudaMemcpyAsync(h->f, h->snap + h->tile_elems, te, cudaMemcpyDeviceToDevice, h->st));
-    CK(h, cudaMemcpyAsync(h->zp, h->snap + 2 * h->tile_elems, 2 * te, cudaMemcpyDeviceToDevice, h->st));
+    CK(h, cudaMemcpyAsync(h->x, snap, te, cudaMemcpyDeviceToDevice, h->st));
+    CK(h, cudaMemcpyAsync(h->f, snap + te, te, cudaMemcpyDeviceToDevice, h->st));
+    CK(h, cudaMemcpyAsync(h->zp, snap + 2 * te, 2 * te, cudaMemcpyDeviceToDevice, h->st));
     CK(h, cudaStreamSynchronize(h->st));
     dfree(h, h->sp_idx[nx]);
     dfree(h, h->sp_val[nx]);
     const int64_t cap = (int64_t)top + (int64_t)top / 2 + 1024;
     h->sp_idx[nx] = (uint32_t*)dalloc(h, (size_t)cap * sizeof(uint32_t));
-    h->sp_val[nx] = (double*)dalloc(h, (size_t)cap * sizeof(double));
+    h->sp_val[nx] = dalloc(h, (size_t)cap * sizeof(T));
     if (!h->sp_idx[nx] || !h->sp_val[nx]) return fail(h, CC_ERR_OOM, "sparse dual pool");
     h->sp_cap[nx] = cap;
     ++h->sp_retries;
   }
   return fail(h, CC_ERR_OOM, "sparse dual pool keeps overflowing");
 }
+
+int sweep_sparse(cc_handle* h) { return h->fp32 ? sweep_sparse_t<float>(h) : sweep_sparse_t<double>(h); }
 
 int launch_sweep(cc_handle* h) {
   void* k = sweep_kernel(h);
@@ -622,7 +627,7 @@ int alloc_sparse(cc_handle* h) {
   const int64_t cap = h->o.pool_entries > 0 ? h->o.pool_entries : std::max<int64_t>((int64_t)1 << 20, (int64_t)h->nbt / 2);
   for (int p = 0; p < 2; ++p) {
     h->sp_idx[p] = (uint32_t*)dalloc(h, (size_t)cap * sizeof(uint32_t));
-    h->sp_val[p] = (double*)dalloc(h, (size_t)cap * sizeof(double));
+    h->sp_val[p] = dalloc(h, (size_t)cap * h->esz);
     h->sp_off[p] = (long long*)dalloc(h, (size_t)h->nbt * sizeof(long long));
     h->sp_cnt[p] = (int*)dalloc(h, (size_t)h->nbt * sizeof(int));
     if (!h->sp_idx[p] || !h->sp_val[p] || !h->sp_off[p] || !h->sp_cnt[p]) return fail(h, CC_ERR_OOM, "sparse dual pools");
@@ -632,6 +637,7 @@ int alloc_sparse(cc_handle* h) {
   }
   const size_t scratch = (size_t)h->sweep_grid * 3 * h->B * h->B * h->B;
   h->sp_scratch = (double*)dalloc(h, scratch * sizeof(double));
+  h->sp_scratch_ctas = h->sweep_grid;
   h->sp_top = (unsigned long long*)dalloc(h, sizeof(unsigned long long));
   h->snap = (double*)dalloc(h, (size_t)h->tile_elems * 4 * sizeof(double));
   if (!h->sp_scratch || !h->sp_top || !h->snap) return fail(h, CC_ERR_OOM, "sparse store scratch");
@@ -769,9 +775,8 @@ int check_opts(const cc_opts& o) {
   if (o.store != CC_STORE_DENSE && o.store != CC_STORE_SPARSE) return fail(nullptr, CC_ERR_ARG, "unknown store");
   if (o.pool_entries < 0) return fail(nullptr, CC_ERR_ARG, "pool_entries must be >= 0");
   if (o.store == CC_STORE_SPARSE &&
-      (o.schedule != CC_SCHED_TILED || o.exact || o.precision != CC_PREC_FP64 ||
-       (o.variant != 0 && o.variant != 3 && o.variant != 4)))
-    return fail(nullptr, CC_ERR_UNSUPPORTED, "the sparse store runs the tiled schedule, fused form, FP64, variant 0, 3 or 4");
+      (o.schedule != CC_SCHED_TILED || o.exact || (o.variant != 0 && o.variant != 3 && o.variant != 4)))
+    return fail(nullptr, CC_ERR_UNSUPPORTED, "the sparse store runs the tiled schedule, fused form, variant 0, 3 or 4");
   return CC_OK;
 }
 
@@ -817,12 +822,22 @@ int resync_fp64(cc_handle* h) {
   const int* bo = h->bt_off;
   Ctl* ctl = h->ctl;
   long long tns = (long long)(h->o.barrier_timeout_s * 1e9);
-  void* args[] = {(void*)&zt, (void*)&mask, (void*)&x, &n, &nb, (void*)&bl, (void*)&bo, (void*)&ctl, &tns};
+  SparseIn sp{};
+  if (h->sparse) {
+    const int c = h->sp_cur;
+    sp.idx = h->sp_idx[c];
+    sp.val = (const double*)h->sp_val[c];
+    sp.off = h->sp_off[c];
+    sp.cnt = h->sp_cnt[c];
+    sp.scratch = (double*)h->sp_scratch;
+  }
+  void* args[] = {(void*)&zt, (void*)&mask, (void*)&x, &n, &nb, (void*)&bl, (void*)&bo, (void*)&ctl, &tns, &sp};
   void* k = B == 8 ? (void*)k_resync_metric<8> : B == 16 ? (void*)k_resync_metric<16> : (void*)k_resync_metric<32>;
   const int threads = threads_for_tile(B);
   int per_sm = 0;
   CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, 0));
-  const int grid = std::max(1, std::min(per_sm * h->sms, std::max(1, h->max_bt_phase)));
+  int grid = std::max(1, std::min(per_sm * h->sms, std::max(1, h->max_bt_phase)));
+  if (h->sparse) grid = std::min(grid, h->sweep_grid);   // one scratch block per CTA
   CK(h, cudaLaunchCooperativeKernel(k, grid, threads, args, 0, h->st));
   k_resync_finish<<<grid_for(h, h->tile_elems, 256), 256, 0, h->st>>>(x, (double*)h->f, h->winv64,
                                                                        (const double*)h->zp, h->ntiles, B * B,
@@ -837,25 +852,53 @@ int switch_to_fp64(cc_handle* h) {
   int rc = read_ctl_error(h);
   if (rc) return rc;
   const size_t te = (size_t)h->tile_elems;
-  double* zt = (double*)dalloc(h, (size_t)h->zt_elems * sizeof(double));
+  double* zt = h->sparse ? nullptr : (double*)dalloc(h, (size_t)h->zt_elems * sizeof(double));
   double* zp = (double*)dalloc(h, te * 2 * sizeof(double));
   double* x = (double*)dalloc(h, te * sizeof(double));
   double* f = (double*)dalloc(h, te * sizeof(double));
-  if (!zt || !zp || !x || !f) {
-    dfree(h, zt); dfree(h, zp); dfree(h, x); dfree(h, f);
+  double* pv[2] = {nullptr, nullptr};
+  if (h->sparse) {
+    pv[0] = (double*)dalloc(h, (size_t)h->sp_cap[0] * sizeof(double));
+    pv[1] = (double*)dalloc(h, (size_t)h->sp_cap[1] * sizeof(double));
+  }
+  if ((!zt && !h->sparse) || !zp || !x || !f || (h->sparse && (!pv[0] || !pv[1]))) {
+    dfree(h, zt); dfree(h, zp); dfree(h, x); dfree(h, f); dfree(h, pv[0]); dfree(h, pv[1]);
     return fail(h, CC_ERR_OOM, "FP64 refinement state");
   }
-  k_convert<float, double><<<grid_for(h, h->zt_elems, 256), 256, 0, h->st>>>((const float*)h->zt, zt, h->zt_elems);
+  if (h->sparse) {   // the current pool's values to FP64; the other pool is rewritten by the next sweep
+    const int c = h->sp_cur;
+    if (h->sp_nnz > 0)
+      k_convert<float, double><<<grid_for(h, h->sp_nnz, 256), 256, 0, h->st>>>((const float*)h->sp_val[c], pv[c],
+                                                                             h->sp_nnz);
+  } else {
+    k_convert<float, double><<<grid_for(h, h->zt_elems, 256), 256, 0, h->st>>>((const float*)h->zt, zt, h->zt_elems);
+  }
   k_convert<float, double><<<grid_for(h, 2 * te, 256), 256, 0, h->st>>>((const float*)h->zp, zp, 2 * (int64_t)te);
   CK(h, cudaGetLastError());
   CK(h, cudaStreamSynchronize(h->st));
   dfree(h, h->zt); dfree(h, h->zp); dfree(h, h->x); dfree(h, h->f); dfree(h, h->d); dfree(h, h->winv);
   h->zt = zt; h->zp = zp; h->x = x; h->f = f; h->d = h->d64; h->winv = h->winv64;
+  if (h->sparse) {
+    dfree(h, h->sp_val[0]);
+    dfree(h, h->sp_val[1]);
+    h->sp_val[0] = pv[0];
+    h->sp_val[1] = pv[1];
+  }
   h->fp32 = false;
   h->esz = 8;
   rc = resync_fp64(h);
   if (rc) return rc;
-  return configure_sweep(h);
+  rc = configure_sweep(h);
+  if (rc) return rc;
+  if (h->sparse && h->sweep_grid > h->sp_scratch_ctas) {   // FP64 grid wider than the FP32 one
+    const size_t scratch = (size_t)h->sweep_grid * 3 * h->B * h->B * h->B;
+    dfree(h, h->sp_scratch);
+    h->sp_scratch = (double*)dalloc(h, scratch * sizeof(double));
+    if (!h->sp_scratch) return fail(h, CC_ERR_OOM, "sparse store scratch");
+    h->sp_scratch_ctas = h->sweep_grid;
+    CK(h, cudaMemsetAsync(h->sp_scratch, 0, scratch * sizeof(double), h->st));
+  }
+  return CC_OK;
 }
 
 // Message for cc_last_error(NULL) from entry points outside this file.
@@ -1132,11 +1175,15 @@ static int move_duals(cc_handle* h, double* y_tri, double* y_pair, int64_t first
         CK(h, cudaMemsetAsync(h->stage, 0, 3 * m * sizeof(double), h->st));
         const int gw = grid_for(h, h->nbt, 128);
         const int c = h->sp_cur;
-#define LAUNCH_SP(BV)                                                                                          \
-  k_tri_duals_sparse<BV><<<gw, 128, 0, h->st>>>(h->sp_idx[c], h->sp_val[c], h->sp_off[c], h->sp_cnt[c],        \
-                                               h->bt_list, h->nbt, (int)h->n, h->ilab, first + c0, m, h->stage, \
-                                               scale);
-        if (h->B == 8) { LAUNCH_SP(8) } else if (h->B == 16) { LAUNCH_SP(16) } else { LAUNCH_SP(32) }
+#define LAUNCH_SP(T, BV)                                                                                       \
+  k_tri_duals_sparse<T, BV><<<gw, 128, 0, h->st>>>(h->sp_idx[c], (const T*)h->sp_val[c], h->sp_off[c],          \
+                                                  h->sp_cnt[c], h->bt_list, h->nbt, (int)h->n, h->ilab,         \
+                                                  first + c0, m, h->stage, scale);
+        if (h->fp32) {
+          if (h->B == 8) { LAUNCH_SP(float, 8) } else if (h->B == 16) { LAUNCH_SP(float, 16) } else { LAUNCH_SP(float, 32) }
+        } else {
+          if (h->B == 8) { LAUNCH_SP(double, 8) } else if (h->B == 16) { LAUNCH_SP(double, 16) } else { LAUNCH_SP(double, 32) }
+        }
 #undef LAUNCH_SP
         CK(h, cudaGetLastError());
         CK(h, cudaMemcpyAsync(y_tri + 3 * c0, h->stage, 3 * m * sizeof(double), cudaMemcpyDeviceToHost, h->st));

@@ -1384,24 +1384,54 @@ __global__ void k_pair_duals_tiled(T* zp, int n, int nb, int B, double* buf, dou
 // disjoint) and inside a block triple sub-phase by sub-phase, so the sums are
 // formed in one fixed order (deterministic); block triples without a nonzero
 // dual are skipped through the bitmask.
+// Sparse-store input of the resync (idx == nullptr: the dense store is used).
+struct SparseIn {
+  const uint32_t* idx;
+  const double* val;
+  const long long* off;
+  const int* cnt;
+  double* scratch;      // 3 B^3 doubles per CTA, zero
+};
+
 template <int B>
 __global__ void __launch_bounds__(TileCfg<B>::NT) k_resync_metric(const double* __restrict__ zt,
                                                                    const uint32_t* __restrict__ mask, double* acc,
                                                                    int n, int nb, const btpk* __restrict__ bt_list,
                                                                    const int* __restrict__ bt_off, Ctl* ctl,
-                                                                   long long timeout_ns) {
+                                                                   long long timeout_ns, SparseIn sp) {
   using C = TileCfg<B>;
   using M = MaskCfg<B>;
   __shared__ double sx[3][C::BB];
+  __shared__ uint32_t smask[M::PER_BT];   // sparse store: the item's bits rebuilt from its entries
   __shared__ int s_flag;
   unsigned target = 0;
   const int lane = threadIdx.x & 31;
+  double* scratch = sp.idx ? sp.scratch + (int64_t)blockIdx.x * (3 * B * C::BB) : nullptr;
   for (int g = 0; g < nb; ++g) {
     for (int w = bt_off[g] + (int)blockIdx.x; w < bt_off[g + 1]; w += gridDim.x) {
-      const uint32_t* mb = mask + (int64_t)w * M::PER_BT;
-      int any = 0;
-      for (int e = threadIdx.x; e < M::PER_BT; e += C::NT) any |= (mb[e] != 0u);
-      if (!__syncthreads_or(any)) continue;
+      const uint32_t* mb;
+      const double* zb;
+      if (sp.idx) {
+        const int m = sp.cnt[w];
+        if (m == 0) continue;   // the same in every thread
+        const long long o = sp.off[w];
+        for (int e = threadIdx.x; e < M::PER_BT; e += C::NT) smask[e] = 0u;
+        __syncthreads();
+        for (int e = threadIdx.x; e < m; e += C::NT) {
+          const uint32_t ix = sp.idx[o + e];
+          atomicOr(&smask[ix >> 5], 1u << (ix & 31));
+          scratch[ix] = sp.val[o + e];
+        }
+        __syncthreads();
+        mb = smask;
+        zb = scratch;
+      } else {
+        mb = mask + (int64_t)w * M::PER_BT;
+        zb = zt + (int64_t)w * (3 * B * C::BB);
+        int any = 0;
+        for (int e = threadIdx.x; e < M::PER_BT; e += C::NT) any |= (mb[e] != 0u);
+        if (!__syncthreads_or(any)) continue;
+      }
       int I, J, K;
       unpack_bt(bt_list[w], I, J, K);
       const int64_t oIJ = tile_index(nb, I, J) * C::BB, oIK = tile_index(nb, I, K) * C::BB,
@@ -1416,7 +1446,6 @@ __global__ void __launch_bounds__(TileCfg<B>::NT) k_resync_metric(const double* 
         if (!ij) sx[2][e] = ld_l2(acc + oJK + e);
       }
       __syncthreads();
-      const double* zb = zt + (int64_t)w * (3 * B * C::BB);
       for (int t = 0; t < B; ++t) {
         for (int q = 0; q < C::SPT; ++q) {
           const int slot = threadIdx.x + q * C::NT;
@@ -1443,6 +1472,10 @@ __global__ void __launch_bounds__(TileCfg<B>::NT) k_resync_metric(const double* 
         acc[oIJ + e] = sx[0][e];
         if (!kj) acc[oIK + e] = sx[1][e];
         if (!ij) acc[oJK + e] = sx[2][e];
+      }
+      if (sp.idx) {   // the scratch block back to zero
+        const long long o = sp.off[w];
+        for (int e = threadIdx.x; e < sp.cnt[w]; e += C::NT) scratch[sp.idx[o + e]] = 0.0;
       }
       __syncthreads();
     }
@@ -1481,8 +1514,8 @@ namespace ccd {
 // ilab maps internal to caller labels (nullptr: identity).  A row is named by
 // the object it leaves out: row 0 (hypotenuse ij) leaves out k, 1 leaves out
 // j, 2 leaves out i.
-template <int B>
-__global__ void k_tri_duals_sparse(const uint32_t* __restrict__ idx, const double* __restrict__ val,
+template <typename T, int B>
+__global__ void k_tri_duals_sparse(const uint32_t* __restrict__ idx, const T* __restrict__ val,
                                    const long long* __restrict__ off, const int* __restrict__ cnt,
                                    const btpk* __restrict__ bt_list, int nbt, int n, const int* __restrict__ ilab,
                                    int64_t first, int64_t count, double* buf, double scale) {
@@ -1508,7 +1541,7 @@ __global__ void k_tri_duals_sparse(const uint32_t* __restrict__ idx, const doubl
       const int u = min(a, min(b, c)), z = max(a, max(b, c)), v = a + b + c - u - z;
       const int row = co == z ? 0 : (co == v ? 1 : 2);
       const int64_t rank = tri_rank(n, u, v, z);
-      if (rank >= first && rank < first + count) buf[3 * (rank - first) + row] = scale * val[o + e];
+      if (rank >= first && rank < first + count) buf[3 * (rank - first) + row] = scale * (double)val[o + e];
     }
   }
 }

@@ -107,7 +107,7 @@ def test_unsupported_combinations_are_refused():
     from paper_1901_10084_gb300 import warmstart
     n = 40
     d, w, _ = planted_partition(n, 2, 0.7, 0.1, seed=1)
-    for kw in (dict(precision="fp32_refine"), dict(exact=True), dict(schedule="summod"),
+    for kw in (dict(exact=True), dict(schedule="summod"),
                dict(schedule="diagonal"), dict(variant=1), dict(variant=2)):
         with pytest.raises(cc.CCError) as e:
             cc.Solver(n, d, w, store="sparse", **kw)
@@ -143,3 +143,33 @@ def test_large_instance_beyond_the_dense_store():
     assert st["max_violation"] < v0
     assert 0 < st["dual_nnz"] < 3 * n * (n - 1) * (n - 2) // 6 // 100
     assert nbytes < 8e9
+
+
+@pytest.mark.parametrize("n,tile,weighted,interleave", [(61, 16, True, True), (150, 8, False, False),
+                                                      (97, 32, True, False)])
+def test_sparse_store_in_the_fp32_bulk_form(n, tile, weighted, interleave):
+    """FP32 bulk sweeps, the FP64 switch (the resync reads the sparse lists in
+    the dense resync's order) and FP64 sweeps after it: the same values as
+    the dense store, bit for bit; the refined solve too."""
+    import paper_1901_10084_gb300 as cc
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=n + 2, weights=(0.5, 2.0) if weighted else None)
+    kw = dict(tile=tile, interleave=interleave, precision="fp32_refine")
+    out = []
+    for store in ("dense", "sparse"):
+        with cc.Solver(n, d, w, store=store, pool_entries=128, **kw) as s:
+            s.sweep(6)
+            a = (*s.get_x(), *s.get_duals())
+            s.refine_fp64()
+            b = (*s.get_x(), *s.get_duals())
+            s.sweep(3)
+            c = (*s.get_x(), *s.get_duals())
+        with cc.Solver(n, d, w, store=store, check_every=5, **kw) as s:
+            conv, k = s.solve(1e-6, 20000)
+            st = s.stats()
+            sol = (conv, k, st["fp32_sweeps"], s.get_x()[0])
+        out.append((a, b, c, sol))
+    for u, v in zip(out[0][:3], out[1][:3]):
+        for p, q in zip(u, v):
+            np.testing.assert_array_equal(p, q)
+    assert out[0][3][:3] == out[1][3][:3] and out[0][3][0]
+    np.testing.assert_array_equal(out[0][3][3], out[1][3][3])
