@@ -280,7 +280,7 @@ def _batched(args, stream):
     inst = batch_planted(args.batch_count, 50, 400, 2, 8, 0.7, 0.05, seed=3)
     T = sum(n * (n - 1) * (n - 2) // 6 for n, _, _ in inst)
     t = time.perf_counter()
-    opts, tune_ms = cc.autotune_batch(inst, trial_sweeps=3)
+    opts, tune_ms = cc.autotune_batch(inst, trial_sweeps=10)
     tune_s = time.perf_counter() - t
     rec = {"instances": len(inst), "triplets_per_sweep": T, "autotuned": opts,
            "autotune_ms_per_sweep": tune_ms, "autotune_seconds": tune_s,
