@@ -706,7 +706,7 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
     item_sync<WARP>();
   }
 
-  // round 1: x tiles and mask words (16-byte copies, L2 only)
+  // first memory round trip: x tiles and mask words (16-byte copies, L2 only)
   constexpr int XCH = C::BB * (int)sizeof(T) / 16;     // 16-byte chunks per tile
   for (int e = tid; e < XCH; e += NTH) {
     cp_async16(reinterpret_cast<char*>(sm.x[0]) + 16 * e, reinterpret_cast<const char*>(a.x + oIJ) + 16 * e);
