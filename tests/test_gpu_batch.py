@@ -71,3 +71,23 @@ def test_autotuner_returns_a_valid_choice():
     with cc.Batch(inst, **opts) as b:
         conv, _, _ = b.solve(1e-4, 3000)
         assert conv
+
+
+def test_full_size_batch_of_256():
+    """The batched configuration at full size (256 planted instances,
+    n ~ U[50, 400], k ~ U[2, 8], p 0.7 / 0.05, seed 3): five batch sweeps give
+    every sampled instance exactly its own handle's iterates."""
+    import paper_1901_10084_gb300 as cc
+    from instances import batch_planted
+    inst = batch_planted(256, 50, 400, 2, 8, 0.7, 0.05, seed=3)
+    with cc.Batch(inst, tile=16) as b:
+        b.sweep(5)
+        for i in range(0, 256, 37):
+            n, d, w = inst[i]
+            with cc.Solver(n, d, w, tile=16) as s:
+                s.sweep(5)
+                xs, fs = s.get_x()
+                ys, _ = s.get_duals()
+            x, f = b.instance(i).get_x()
+            y, _ = b.instance(i).get_duals()
+            assert np.array_equal(x, xs) and np.array_equal(f, fs) and np.array_equal(y, ys)

@@ -312,23 +312,74 @@ def test_barrier_time_limit_reports_and_context_survives():
 
 # ---------------------------------------------------------------- full size
 
-def test_full_size_chunglu1000_one_sweep():
-    """The benchmark workload (n = 1000, tile 16, default launch): one sweep
-    from the initial state in both forms against the oracle; x and f in full,
-    the duals on three sampled ranges."""
+def _caller_triplets(n, first, count):
+    """Caller triplets i<j<k of lexicographic ranks [first, first + count)."""
+    import itertools
+    i = 0
+    while oracle.trank(n, i + 1, i + 2, i + 3) <= first if i + 3 < n else False:
+        i += 1
+    out = []
+    for t in itertools.combinations(range(i, n), 3):
+        r = oracle.trank(n, *t)
+        if r >= first + count:
+            break
+        if r >= first:
+            out.append(t)
+    assert len(out) == count
+    return out
+
+
+def test_full_size_chunglu1000_bench_configuration():
+    """The benchmark workload in the launch configuration bench.py times
+    (tile 16, relabeled objects, default sweep form): three sweeps from the
+    start against the oracle run on the relabeled instance (the first sweep
+    only moves the pair rows; the second and third have many active rows);
+    x and f in full, the duals on three sampled ranges, mapped by hand."""
+    from relabel import deal_labels
+    n, d, w, _ = workload("chunglu1000")
+    B = 16
+    lab = deal_labels(n, B)
+    iu, ju = np.triu_indices(n, 1)
+    a, b = lab[iu], lab[ju]
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    pmap = lo * n - lo * (lo + 1) // 2 + (hi - lo - 1)       # caller pair -> internal pair
+    dint, wint = np.empty_like(d), np.empty_like(w)
+    dint[pmap], wint[pmap] = d, w
+    o = oracle.State(n, dint, wint, 0.2)
+    with _solver(n, d, w, eps=0.2, tile=B, interleave=True) as s:
+        for k in range(3):
+            o.sweep(2, B)
+            s.sweep(1)
+        x, f = s.get_x()
+        assert _rel(x, o.x[pmap]) <= TOL_SWEEP and _rel(f, o.f[pmap]) <= TOL_SWEEP
+        T = n * (n - 1) * (n - 2) // 6
+        for first in (0, T // 2, T - 40000):
+            yt, _ = s.get_duals(first, 40000, pairs=False)
+            ref = np.empty(3 * 40000)
+            for q, (i, j, k) in enumerate(_caller_triplets(n, first, 40000)):
+                li, lj, lk = lab[i], lab[j], lab[k]
+                u, z = min(li, lj, lk), max(li, lj, lk)
+                v = li + lj + lk - u - z
+                base = 3 * oracle.trank(n, u, v, z)
+                for row, out in enumerate((lk, lj, li)):      # caller row ij leaves k out, ik j, jk i
+                    ref[3 * q + row] = o.ytri[base + (0 if out == z else 1 if out == v else 2)]
+            assert _rel(yt, ref) <= TOL_SWEEP
+        st = s.check()
+    assert st["max_violation"] == pytest.approx(o.max_violation(), abs=1e-12)
+
+
+def test_full_size_chunglu1000_exact_two_sweeps():
+    """The exact form at full size, two sweeps from the start (the second with
+    active rows): bit-identical to the oracle."""
     n, d, w, _ = workload("chunglu1000")
     o = oracle.State(n, d, w, 0.2)
     o.sweep(2, 16)
-    T = n * (n - 1) * (n - 2) // 6
-    ranges = [(0, 200000), (T // 2, 200000), (T - 200000, 200000)]
-    for exact in (True, False):
-        with _solver(n, d, w, eps=0.2, tile=16, exact=exact) as s:
-            s.sweep(1)
-            x, f = s.get_x()
-            tol = 0.0 if exact else TOL_SWEEP
-            assert _rel(x, o.x) <= tol and _rel(f, o.f) <= tol
-            for first, count in ranges:
-                yt, _ = s.get_duals(first, count, pairs=False)
-                assert _rel(yt, o.ytri[3 * first: 3 * (first + count)]) <= tol
-            st = s.check()
-            assert st["max_violation"] == pytest.approx(o.max_violation(), abs=1e-12)
+    o.sweep(2, 16)
+    with _solver(n, d, w, eps=0.2, tile=16, exact=True) as s:
+        s.sweep(2)
+        x, f = s.get_x()
+        assert np.array_equal(x, o.x) and np.array_equal(f, o.f)
+        T = n * (n - 1) * (n - 2) // 6
+        for first in (0, T // 2, T - 200000):
+            yt, _ = s.get_duals(first, 200000, pairs=False)
+            assert np.array_equal(yt, o.ytri[3 * first: 3 * (first + 200000)])

@@ -102,3 +102,31 @@ def test_refine_switch_keeps_the_invariant():
     if n <= 130:
         r = dense.invariant_residual(n, d, w, 0.2, x, f, yt2, yp2)
         assert r <= 1e-12
+
+
+def test_full_size_chunglu3000w_fp32_refine():
+    """The weighted n = 3000 configuration in the FP32 bulk form (here on the
+    sparse store, which gives the dense store's values bit for bit and keeps
+    the test at about 1 GB; the oracle needs minutes per sweep at this size,
+    so properties are checked): the FP64 switch rebuilds x consistently with
+    the FP32 state, the refined solve reaches the tolerance, and its LP
+    objective and x agree with a plain FP64 solve."""
+    import paper_1901_10084_gb300 as cc
+    n, d, w, _ = workload("chunglu3000w")
+    with cc.Solver(n, d, w, tile=16, precision="fp32_refine", store="sparse") as s:
+        s.sweep(20)
+        x32, _ = s.get_x()
+        s.refine_fp64()
+        x64, _ = s.get_x()
+        assert np.max(np.abs(x64 - x32)) <= 1e-4 * max(np.max(np.abs(x32)), 1.0)
+    res = {}
+    for prec in ("fp32_refine", "fp64"):
+        with cc.Solver(n, d, w, tile=16, precision=prec, store="sparse", check_every=10) as s:
+            conv, k = s.solve(1e-4, 3000)
+            st = s.check()
+            res[prec] = (conv, st, s.get_x()[0])
+    for prec in res:
+        assert res[prec][0] and res[prec][1]["max_violation"] <= 1e-4
+    lp32, lp64 = res["fp32_refine"][1]["lp_objective"], res["fp64"][1]["lp_objective"]
+    assert abs(lp32 - lp64) <= 1e-4 * abs(lp64)
+    assert np.max(np.abs(res["fp32_refine"][2] - res["fp64"][2])) <= 1e-2
