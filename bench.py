@@ -130,6 +130,25 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# ---------------------------------------------------------------- ranks
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The job's time: the largest per-rank time (all_reduce MAX; NCCL on the
+    GPU, gloo on the CPU in the tests).  dist None: a single process."""
+    if dist is None:
+        return ms
+    import torch
+    tt = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(world: int, steps: int, units_per_step: int, ms: float) -> float:
+    """Whole-job throughput: every rank processes its own replica's units, so
+    the job does world x steps x units in the slowest rank's time (weak scaling)."""
+    return world * steps * units_per_step / (ms * 1e-3)
+
+
 # ---------------------------------------------------------------- our arm
 
 def run_ours(args, rank, world, local_rank):
@@ -185,11 +204,8 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop() if clocks else None
     sweep_ms = [a.elapsed_time(b) for a, b, _ in ev]
     ms = sum(a.elapsed_time(c) for a, _, c in ev)
-    if dist is not None:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * args.steps * T / (ms * 1e-3)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = job_value(world, args.steps, T, ms)
 
     out = None
     if rank == 0:
