@@ -14,6 +14,11 @@
  * A.  One "sweep" visits every row once: the three metric rows of every
  * triplet (hypotenuse ij, then ik, then jk), phase by phase in the chosen
  * schedule (Sec. III-B/C), then the two rows of every pair.
+ * opts.problem = CC_PROB_L2 selects instead l2 metric nearness (Eq.
+ * metricnear with p = 2: the metric rows only, x starting at d), and
+ * opts.store = CC_STORE_SPARSE keeps only the nonzero triangle duals, per
+ * block triple in visiting order (Sec. III-D), for sizes whose dense dual store
+ * would not fit.
  *
  * Layouts of host arrays exchanged through this ABI:
  *   pairs     P = n(n-1)/2 doubles, packed row-major over i<j (0-based):
