@@ -51,7 +51,12 @@ class _TorchAllocator:
         self.device = device
 
         def _alloc(ctx, nbytes, stream):
-            return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, int(stream or 0)))
+            # a failed request must come back as NULL (the library then reports
+            # CC_ERR_OOM); an exception cannot cross the C callback
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, int(stream or 0)))
+            except Exception:
+                return 0
 
         def _free(ctx, ptr, stream):
             torch.cuda.caching_allocator_delete(int(ptr))

@@ -258,7 +258,7 @@ def test_resume_is_exact():
         np.testing.assert_array_equal(g, r)
 
 
-@pytest.mark.parametrize("n,k,eps", [(300, 6, 0.2), (130, 3, 1.0)])
+@pytest.mark.parametrize("n,k,eps", [(300, 6, 0.2), (130, 3, 1.0), (1000, 10, 0.2)])
 def test_closed_form_clustered_on_gpu(n, k, eps):
     d, w, _ = clustered(n, k, seed=1, weights=(0.5, 2.0))
     with _solver(n, d, w, eps=eps, tile=16, check_every=5) as s:
