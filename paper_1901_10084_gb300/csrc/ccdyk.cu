@@ -377,7 +377,15 @@ int sweep_sparse_t(cc_handle* h) {
     const int64_t cap = (int64_t)top + (int64_t)top / 2 + 1024;
     h->sp_idx[nx] = (uint32_t*)dalloc(h, (size_t)cap * sizeof(uint32_t));
     h->sp_val[nx] = dalloc(h, (size_t)cap * sizeof(T));
-    if (!h->sp_idx[nx] || !h->sp_val[nx]) return fail(h, CC_ERR_OOM, "sparse dual pool");
+    if (!h->sp_idx[nx] || !h->sp_val[nx]) {
+      // capacity 0: a later sweep overflows again and writes nothing
+      dfree(h, h->sp_idx[nx]);
+      dfree(h, h->sp_val[nx]);
+      h->sp_idx[nx] = nullptr;
+      h->sp_val[nx] = nullptr;
+      h->sp_cap[nx] = 0;
+      return fail(h, CC_ERR_OOM, "sparse dual pool");
+    }
     h->sp_cap[nx] = cap;
     ++h->sp_retries;
   }
