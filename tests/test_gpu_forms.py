@@ -107,3 +107,30 @@ def test_first_sweep_shortcut_is_exact(store, n, tile, weighted):
         c = _run(n, d, w, 3, **kw)
         for u, v in zip(b[:4], c[:4]):
             assert np.array_equal(u, v)
+
+
+def test_random_configurations_equal_the_unfiltered_sweep():
+    """Seeded fuzzing of the exactness claim: random sizes (including tiny and
+    ragged ones), tiles, weights, relabeling, problems, stores and precision
+    forms; the default sweep must equal the unfiltered one bit for bit."""
+    from instances import random_dissimilarity
+    rng = np.random.default_rng(2024)
+    for case in range(24):
+        problem = "l2" if rng.random() < 0.3 else "cc"
+        n = int(rng.choice([3, 4, 5, 17, 33, 64, 65, 97, 130, 211]))
+        tile = int(rng.choice([8, 16, 32]))
+        weighted = bool(rng.random() < 0.5)
+        store = "sparse" if rng.random() < 0.4 else "dense"
+        precision = "fp32_refine" if (problem == "cc" and rng.random() < 0.3) else "fp64"
+        interleave = bool(rng.random() < 0.5)
+        sweeps = int(rng.integers(1, 12))
+        seed = int(rng.integers(0, 10**6))
+        if problem == "l2":
+            d, w = random_dissimilarity(n, seed, weights=(0.5, 2.0) if weighted else None)
+        else:
+            d, w, _ = chung_lu(n, 2.5, 8.0, seed=seed, weights=(0.5, 2.0) if weighted else None)
+        kw = dict(tile=tile, interleave=interleave, problem=problem, precision=precision, store=store)
+        a = _run(n, d, w, sweeps, variant=0, **kw)
+        b = _run(n, d, w, sweeps, variant=4, **kw)
+        for u, v in zip(a[:4], b[:4]):
+            assert np.array_equal(u, v), (case, kw, n, sweeps)
