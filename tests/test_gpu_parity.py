@@ -383,3 +383,39 @@ def test_full_size_chunglu1000_exact_two_sweeps():
         for first in (0, T // 2, T - 200000):
             yt, _ = s.get_duals(first, 200000, pairs=False)
             assert np.array_equal(yt, o.ytri[3 * first: 3 * (first + 200000)])
+
+
+def test_random_configurations_track_the_oracle():
+    """Seeded fuzzing against the oracle: random problem (CC LP or l2),
+    schedule, form, tile, size (tiny and ragged included) and weights; a few
+    sweeps from the start.  The exact form must equal the oracle bit for bit,
+    the fused form stay within 1e-11 (a few sweeps of 1e-12 rounding)."""
+    from instances import random_dissimilarity
+    rng = np.random.default_rng(77)
+    for case in range(20):
+        problem = "l2" if rng.random() < 0.35 else "cc"
+        schedule = int(rng.choice([0, 1, 2, 2]))
+        exact = bool(rng.random() < 0.5)
+        n = int(rng.choice([3, 4, 9, 20, 33, 48, 61, 80]))
+        tile = int(rng.choice([8, 16, 32]))
+        weighted = bool(rng.random() < 0.5)
+        sweeps = int(rng.integers(1, 5))
+        seed = int(rng.integers(0, 10**6))
+        if problem == "l2":
+            d, w = random_dissimilarity(n, seed, weights=(0.5, 2.0) if weighted else None)
+            o = oracle.State(n, d, w, problem="l2")
+        else:
+            d, w, _ = chung_lu(n, 2.5, 8.0, seed=seed, weights=(0.5, 2.0) if weighted else None)
+            o = oracle.State(n, d, w, 0.2)
+        with _solver(n, d, w, eps=0.2, schedule=schedule, tile=tile, exact=exact, problem=problem) as s:
+            s.sweep(sweeps)
+            for _ in range(sweeps):
+                o.sweep(schedule, tile)
+            g = _gpu_state(s)
+        what = (case, problem, schedule, exact, n, tile, weighted, sweeps)
+        if exact:
+            for u, v in zip(g, (o.x, o.f, o.ytri, o.ypair)):
+                assert np.array_equal(u, v), what
+        else:
+            for u, v in zip(g, (o.x, o.f, o.ytri, o.ypair)):
+                assert _rel(u, v) <= 1e-11, what
