@@ -379,21 +379,25 @@ int cc_ws_samples(cc_handle* h, float* feat, float* target, int64_t cap, int64_t
  * Synchronous on `stream` (cudaStream_t; NULL = legacy default stream). */
 int cc_mlp_forward(const float* params, const float* feat, float* out, int64_t count, void* stream);
 
-/* Gradient of the mean squared error L = sum_q sum_r (out[q][r] - target[q][r])^2
- * / (3 count) over all count rows (feat, target: device; params, grad
+/* Gradient of the weighted mean squared error
+ * L = sum_q sum_r v(target[q][r]) (out[q][r] - target[q][r])^2 / (3 count)
+ * over all count rows, v(t) = pos_weight for t > 0 and 1 otherwise (1 gives
+ * the plain mean squared error; feat, target: device; params, grad
  * (CC_WS_NPARAM floats), loss (nullable): host).  Same arithmetic as one
- * training step (BF16 operands, FP32 accumulation).  Synchronous. */
-int cc_mlp_grad(const float* params, const float* feat, const float* target, int64_t count, float* grad, float* loss,
-                void* stream);
+ * training step (BF16 operands, FP32 accumulation).  CC_ERR_ARG when
+ * pos_weight is not positive and finite.  Synchronous. */
+int cc_mlp_grad(const float* params, const float* feat, const float* target, int64_t count, float pos_weight,
+                float* grad, float* loss, void* stream);
 
 /* `steps` Adam steps (beta 0.9 / 0.999, eps 1e-8, learning rate lr, FP32
  * master weights) on minibatches of `batch` rows drawn uniformly with
  * replacement (SplitMix64 of seed, step and row) from the count rows of
  * feat / target (device).  params (host) holds the initial weights and
  * receives the trained ones; loss (host, nullable): `steps` floats, the
- * minibatch loss before each step.  Synchronous. */
+ * minibatch loss before each step.  The loss is cc_mlp_grad's with the
+ * same pos_weight.  Synchronous. */
 int cc_mlp_train(float* params, const float* feat, const float* target, int64_t count, int32_t batch, int32_t steps,
-                 float lr, uint64_t seed, float* loss, void* stream);
+                 float lr, uint64_t seed, float pos_weight, float* loss, void* stream);
 
 /* Release everything the handle owns.  NULL is a no-op. */
 void cc_destroy(cc_handle* h);

@@ -184,10 +184,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         lib.cc_ws_samples.restype = ctypes.c_int
         lib.cc_mlp_forward.argtypes = [fp, vp, vp, i64, vp]
         lib.cc_mlp_forward.restype = ctypes.c_int
-        lib.cc_mlp_grad.argtypes = [fp, vp, vp, i64, fp, fp, vp]
+        lib.cc_mlp_grad.argtypes = [fp, vp, vp, i64, ctypes.c_float, fp, fp, vp]
         lib.cc_mlp_grad.restype = ctypes.c_int
         lib.cc_mlp_train.argtypes = [fp, vp, vp, i64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
-                                     ctypes.c_uint64, fp, vp]
+                                     ctypes.c_uint64, ctypes.c_float, fp, vp]
         lib.cc_mlp_train.restype = ctypes.c_int
         _lib = lib
         return lib
@@ -424,25 +424,26 @@ def cc_mlp_forward(params, feat_ptr: int, out_ptr: int, count: int, stream: int 
     _check(load().cc_mlp_forward(_fp(p), v(feat_ptr), v(out_ptr), count, v(stream)), None)
 
 
-def cc_mlp_grad(params, feat_ptr: int, target_ptr: int, count: int, stream: int = 0):
+def cc_mlp_grad(params, feat_ptr: int, target_ptr: int, count: int, pos_weight: float = 1.0, stream: int = 0):
     """Returns (gradient as float32 array, loss)."""
     import numpy as np
     p = _params(params)
     g = np.zeros(CC_WS_NPARAM, dtype=np.float32)
     loss = ctypes.c_float(0.0)
     v = ctypes.c_void_p
-    _check(load().cc_mlp_grad(_fp(p), v(feat_ptr), v(target_ptr), count, _fp(g), ctypes.byref(loss), v(stream)),
+    _check(load().cc_mlp_grad(_fp(p), v(feat_ptr), v(target_ptr), count, pos_weight, _fp(g), ctypes.byref(loss),
+                              v(stream)),
            None)
     return g, float(loss.value)
 
 
 def cc_mlp_train(params, feat_ptr: int, target_ptr: int, count: int, batch: int, steps: int, lr: float,
-                 seed: int, stream: int = 0):
+                 seed: int, pos_weight: float = 1.0, stream: int = 0):
     """Returns (trained params, per-step minibatch losses); params is not modified."""
     import numpy as np
     p = _params(params).copy()
     losses = np.zeros(max(steps, 0), dtype=np.float32)
     v = ctypes.c_void_p
-    _check(load().cc_mlp_train(_fp(p), v(feat_ptr), v(target_ptr), count, batch, steps, lr, seed,
+    _check(load().cc_mlp_train(_fp(p), v(feat_ptr), v(target_ptr), count, batch, steps, lr, seed, pos_weight,
                                _fp(losses) if steps > 0 else None, v(stream)), None)
     return p, losses

@@ -1903,6 +1903,7 @@ cudaError_t ws_train_alloc(WsTrainBufs& b, int steps, cudaStream_t st) {
 }
 
 cudaError_t ws_train_launch(const WsTrainBufs& b, const float* feat, const float* target, int64_t count, int64_t rows,
+                            float pos_weight,
                             int sample, uint64_t seed, float* loss, cudaStream_t st) {
   const size_t smem = sizeof(WsTrainSmem);
   cudaError_t e = cudaFuncSetAttribute(k_ws_train_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1912,7 +1913,8 @@ cudaError_t ws_train_launch(const WsTrainBufs& b, const float* feat, const float
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t chunks = (rows + 15) / 16;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((chunks + WS_TRAIN_WARPS - 1) / WS_TRAIN_WARPS, sms));
-  k_ws_train_grad<<<grid, 32 * WS_TRAIN_WARPS, smem, st>>>(b.p, feat, target, count, rows, sample, seed, b.g, loss);
+  k_ws_train_grad<<<grid, 32 * WS_TRAIN_WARPS, smem, st>>>(b.p, feat, target, count, rows, sample, seed, pos_weight,
+                                                           b.g, loss);
   return cudaGetLastError();
 }
 
@@ -1920,14 +1922,15 @@ cudaError_t ws_train_launch(const WsTrainBufs& b, const float* feat, const float
 
 extern "C" {
 
-int cc_mlp_grad(const float* params, const float* feat, const float* target, int64_t count, float* grad, float* loss,
-                void* stream) {
+int cc_mlp_grad(const float* params, const float* feat, const float* target, int64_t count, float pos_weight,
+                float* grad, float* loss, void* stream) {
   if (!params || !feat || !target || !grad || count <= 0) return fail(nullptr, CC_ERR_ARG, "NULL argument or count <= 0");
+  if (!(pos_weight > 0.f && pos_weight < INFINITY)) return fail(nullptr, CC_ERR_ARG, "pos_weight not positive and finite");
   cudaStream_t st = (cudaStream_t)stream;
   WsTrainBufs b;
   cudaError_t e = ws_train_alloc(b, 1, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b.p, params, WS_NPARAM * sizeof(float), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = ws_train_launch(b, feat, target, count, count, 0, 0, b.loss, st);
+  if (e == cudaSuccess) e = ws_train_launch(b, feat, target, count, count, pos_weight, 0, 0, b.loss, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(grad, b.g, WS_NPARAM * sizeof(float), cudaMemcpyDeviceToHost, st);
   float l = 0.f;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&l, b.loss, sizeof(float), cudaMemcpyDeviceToHost, st);
@@ -1939,16 +1942,17 @@ int cc_mlp_grad(const float* params, const float* feat, const float* target, int
 }
 
 int cc_mlp_train(float* params, const float* feat, const float* target, int64_t count, int32_t batch, int32_t steps,
-                 float lr, uint64_t seed, float* loss, void* stream) {
+                 float lr, uint64_t seed, float pos_weight, float* loss, void* stream) {
   if (!params || !feat || !target || count <= 0 || batch <= 0 || steps < 0 || !(lr > 0.f))
     return fail(nullptr, CC_ERR_ARG, "NULL argument, count/batch <= 0, steps < 0 or lr <= 0");
+  if (!(pos_weight > 0.f && pos_weight < INFINITY)) return fail(nullptr, CC_ERR_ARG, "pos_weight not positive and finite");
   if (steps == 0) return CC_OK;
   cudaStream_t st = (cudaStream_t)stream;
   WsTrainBufs b;
   cudaError_t e = ws_train_alloc(b, steps, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b.p, params, WS_NPARAM * sizeof(float), cudaMemcpyHostToDevice, st);
   for (int s = 0; s < steps && e == cudaSuccess; ++s) {
-    e = ws_train_launch(b, feat, target, count, batch, 1, seed * 1000003ull + (uint64_t)s, b.loss + s, st);
+    e = ws_train_launch(b, feat, target, count, batch, pos_weight, 1, seed * 1000003ull + (uint64_t)s, b.loss + s, st);
     if (e == cudaSuccess) {
       k_ws_adam<<<(WS_NPARAM + 255) / 256, 256, 0, st>>>(b.p, b.m, b.v, b.g, lr, 0.9f, 0.999f, 1e-8f, s + 1);
       e = cudaGetLastError();

@@ -353,7 +353,7 @@ __device__ __forceinline__ void ws_bfrag_rows(const __nv_bfloat16* m, int nb, in
 // against the targets, summed into grad (global), loss into *loss.
 __global__ void __launch_bounds__(32 * WS_TRAIN_WARPS) k_ws_train_grad(
     const float* __restrict__ params, const float* __restrict__ feat, const float* __restrict__ target,
-    int64_t count, int64_t rows, int sample, uint64_t seed, float* grad, float* loss) {
+    int64_t count, int64_t rows, int sample, uint64_t seed, float pos_weight, float* grad, float* loss) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WsTrainSmem& S = *reinterpret_cast<WsTrainSmem*>(smem_raw);
   ws_stage_weights(params, S.w);
@@ -394,8 +394,9 @@ __global__ void __launch_bounds__(32 * WS_TRAIN_WARPS) k_ws_train_grad(
         const float y = target[rowi[row] * 3 + col];
         const float p = softplus(o[q]);
         const float sig = 1.f / (1.f + expf(-o[q]));
-        dO[q] = 2.f * (p - y) * scale * sig;
-        lsum += (p - y) * (p - y) * scale;
+        const float wt = y > 0.f ? pos_weight : 1.f;   // weight of the nonzero targets
+        dO[q] = 2.f * (p - y) * scale * sig * wt;
+        lsum += wt * (p - y) * (p - y) * scale;
       }
     }
     for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);

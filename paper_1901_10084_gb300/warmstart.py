@@ -85,19 +85,21 @@ def forward(params, feat: torch.Tensor) -> torch.Tensor:
     return out
 
 
-def grad(params, feat: torch.Tensor, target: torch.Tensor):
-    """Full-batch (gradient, loss) of the mean squared error."""
+def grad(params, feat: torch.Tensor, target: torch.Tensor, pos_weight=1.0):
+    """Full-batch (gradient, loss) of the mean squared error, the terms of
+    positive targets weighted by ``pos_weight``."""
     feat, target = feat.contiguous(), target.contiguous()
-    return _native.cc_mlp_grad(params, feat.data_ptr(), target.data_ptr(), feat.shape[0],
+    return _native.cc_mlp_grad(params, feat.data_ptr(), target.data_ptr(), feat.shape[0], pos_weight,
                                torch.cuda.current_stream(feat.device).cuda_stream)
 
 
-def train(feat: torch.Tensor, target: torch.Tensor, steps=2000, batch=4096, lr=3e-3, seed=0, params=None):
-    """Adam on minibatches; returns (params, per-step losses)."""
+def train(feat: torch.Tensor, target: torch.Tensor, steps=2000, batch=4096, lr=3e-3, seed=0, params=None,
+          pos_weight=1.0):
+    """Adam on minibatches of ``grad``'s loss; returns (params, per-step losses)."""
     feat, target = feat.contiguous(), target.contiguous()
     p0 = init_params(seed) if params is None else params
     return _native.cc_mlp_train(p0, feat.data_ptr(), target.data_ptr(), feat.shape[0], batch, steps, lr, seed,
-                                torch.cuda.current_stream(feat.device).cuda_stream)
+                                pos_weight, torch.cuda.current_stream(feat.device).cuda_stream)
 
 
 def collect_batch(instances, eps=0.2, tol=1e-4, max_sweeps=20000, tile=16, device=0, group=256):

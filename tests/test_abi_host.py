@@ -79,10 +79,14 @@ def test_warm_start_calls_reject_null_arguments(lib):
     assert lib.cc_ws_samples(None, None, None, 0, None) == N.CC_ERR_ARG
     assert lib.cc_mlp_forward(None, None, None, 4, None) == N.CC_ERR_ARG
     assert lib.cc_mlp_forward(pp, None, None, -1, None) == N.CC_ERR_ARG
-    assert lib.cc_mlp_grad(pp, None, None, 16, pp, None, None) == N.CC_ERR_ARG
-    assert lib.cc_mlp_train(pp, None, None, 16, 16, 1, 1e-3, 0, None, None) == N.CC_ERR_ARG
-    assert lib.cc_mlp_train(pp, ctypes.c_void_p(16), ctypes.c_void_p(16), 16, 0, 1, 1e-3, 0, None, None) \
+    assert lib.cc_mlp_grad(pp, None, None, 16, 1.0, pp, None, None) == N.CC_ERR_ARG
+    assert lib.cc_mlp_train(pp, None, None, 16, 16, 1, 1e-3, 0, 1.0, None, None) == N.CC_ERR_ARG
+    assert lib.cc_mlp_train(pp, ctypes.c_void_p(16), ctypes.c_void_p(16), 16, 0, 1, 1e-3, 0, 1.0, None, None) \
         == N.CC_ERR_ARG
+    dev = ctypes.c_void_p(16)    # never dereferenced: the weight check fails first
+    for wt in (0.0, -1.0, float("inf"), float("nan")):
+        assert lib.cc_mlp_grad(pp, dev, dev, 16, wt, pp, None, None) == N.CC_ERR_ARG
+        assert lib.cc_mlp_train(pp, dev, dev, 16, 16, 1, 1e-3, 0, wt, None, None) == N.CC_ERR_ARG
 
 
 def test_warm_start_parameter_count_matches_the_network():

@@ -107,14 +107,18 @@ def test_forward_of_empty_input():
     assert out.shape == (0, 3)
 
 
-@pytest.mark.parametrize("count", [16, 333, 2048])
-def test_gradient_matches_fp32_autograd(count):
+@pytest.mark.parametrize("count,pos_weight", [(16, 1.0), (333, 1.0), (2048, 1.0), (333, 4.0), (2048, 0.25)])
+def test_gradient_matches_fp32_autograd(count, pos_weight):
+    """The weighted loss: terms of positive targets (half of them here) count
+    pos_weight times, the zero targets once."""
     torch = _torch()
     from paper_1901_10084_gb300 import warmstart
     params = warmstart.init_params(seed=7, out_bias=-0.5)
     feat = torch.tensor(_sample_features(count, 100 + count))
-    target = torch.tensor(np.random.default_rng(count).exponential(0.3, (count, 3)).astype(np.float32))
-    g, loss = warmstart.grad(params, feat.cuda(), target.cuda())
+    rng = np.random.default_rng(count)
+    t = rng.exponential(0.3, (count, 3)) * (rng.random((count, 3)) < 0.5)
+    target = torch.tensor(t.astype(np.float32))
+    g, loss = warmstart.grad(params, feat.cuda(), target.cuda(), pos_weight=pos_weight)
     p = torch.tensor(params, requires_grad=True)
     parts, o = [], 0
     for size in (5 * 64, 64, 64 * 64, 64, 64 * 3, 3):
@@ -126,7 +130,8 @@ def test_gradient_matches_fp32_autograd(count):
     h1 = x @ W1 + b1
     h2 = torch.relu(h1) @ W2 + b2
     out = torch.nn.functional.softplus(torch.relu(h2) @ W3 + b3)
-    ref_loss = ((out - target) ** 2).mean()
+    v = torch.where(target > 0, torch.tensor(pos_weight), torch.tensor(1.0))
+    ref_loss = (v * (out - target) ** 2).mean()
     ref_loss.backward()
     gref = p.grad.numpy()
     assert abs(loss - ref_loss.item()) <= 2e-2 * ref_loss.item()
