@@ -543,49 +543,65 @@ def _time_to_tol(args, n, d, w, stream, precision):
 
 # ---------------------------------------------------------------- oracle
 
-def cpu_baseline(workload_name, rows_fraction=1.0):
-    """Time the oracle (as it stands, one host thread) on one sweep's first
-    rows_fraction of metric rows of the workload."""
+def cpu_baseline(workload_name):
+    """Time the oracle as it stands on one sweep of the workload: its
+    threaded form on every host core (the units of each phase dealt to the
+    threads; bitwise the serial sweep), and the serial form on one core."""
     import oracle
     from instances import workload
     n, d, w, desc = workload(workload_name)
     T = n * (n - 1) * (n - 2) // 6
+    cores = os.cpu_count() or 1
     st = oracle.State(n, d, w, 0.2)
-    rows = int(3 * T * rows_fraction)
     t = time.perf_counter()
-    st.sweep(2, 16, max_rows=rows)
+    st.sweep_threads(2, 16, cores)
     el = time.perf_counter() - t
-    return {"value": rows / 3 / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {rows} metric rows ({rows_fraction:g} of a sweep) of {desc}, tiled "
-                      f"schedule B=16, serial C oracle, {el:.1f} s"}
+    st = oracle.State(n, d, w, 0.2)
+    t = time.perf_counter()
+    st.sweep(2, 16)
+    el1 = time.perf_counter() - t
+    return {"value": T / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one full sweep (first sweep from the initial state) of {desc}, tiled schedule "
+                      f"B=16, C oracle, units of each phase on {cores} host threads, {el:.2f} s",
+            "serial": {"value": T / el1, "cores": 1, "seconds": el1,
+                       "sample": "the same sweep with the serial C oracle on one host thread"}}
 
 
 def run_reference(args, rank):
+    """The oracle on every host core (threaded form), each step the metric
+    rows of the first q phases of a sweep, q chosen from a one-phase timing
+    so that the whole run takes about two minutes."""
     if rank != 0:
         return None
     import oracle
     from instances import workload
     n, d, w, desc = workload(args.workload)
     T = n * (n - 1) * (n - 2) // 6
-    frac = 1.0 / 8
-    rows = int(3 * T * frac)
+    cores = os.cpu_count() or 1
+    phases = oracle.num_phases(n, 2, args.tile)
     st = oracle.State(n, d, w, 0.2)
+    t = time.perf_counter()
+    st.sweep_threads(2, args.tile, cores, max_phases=1)
+    one = time.perf_counter() - t
+    q = int(max(1, min(phases, 120.0 / max(args.steps + args.warmup, 1) / max(one, 1e-6))))
     for _ in range(args.warmup):
-        st.sweep(2, args.tile, max_rows=rows)
+        st.sweep_threads(2, args.tile, cores, max_phases=q)
+    rows = 0
     t = time.perf_counter()
     for _ in range(args.steps):
-        st.sweep(2, args.tile, max_rows=rows)
+        rows += st.sweep_threads(2, args.tile, cores, max_phases=q)
     el = time.perf_counter() - t
-    value = args.steps * rows / 3 / el
-    sample = (f"each step: the first 1/8 of one sweep's metric rows ({rows} rows) of {desc}, tiled "
-              f"schedule B={args.tile}, serial C oracle on one host core")
+    value = rows / 3 / el
+    sample = (f"each step: the metric rows of the first {q} of the {phases} phases of one sweep "
+              f"({rows // 3 // max(args.steps, 1)} triplets) of {desc}, tiled schedule B={args.tile}, "
+              f"C oracle with the units of each phase on {cores} host threads")
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": args.workload, "desc": desc, "n": n, "triplets": T,
                        "schedule": "tiled", "tile": args.tile, "precision": "fp64"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
 

@@ -7,7 +7,9 @@ with it.
 
 ``dykstra.c`` is a plain serial FP64 transcription of Algorithm 1 specialised
 to the metric rows of Eq. (mn1) (Sec. II-B) and walked in the schedules of
-Sec. III-B/C; ``dense.py`` holds brute-force checks built from a dense
+Sec. III-B/C, with a threaded form of the same sweep that deals the disjoint
+units of each phase to host threads (the parallelism of Sec. III-A/C; the
+result equals the serial sweep bit for bit); ``dense.py`` holds brute-force checks built from a dense
 constraint matrix (an LP solve with HiGHS, A^T y, a KKT certificate).
 
 Parity status of each function:
@@ -15,6 +17,8 @@ Parity status of each function:
     projection property, the worked triangle case of Sec. II-B, the invariant
     v = v0 - W^{-1} A^T y / eps, monotone dual objective, KKT at convergence,
     dense LP at small n, the closed-form clustered instance).
+  * ``sweep_threads``: pinned to the serial sweep, bit for bit, for every
+    schedule, thread count and partial sweep in ``tests/test_oracle_threads.py``.
   * ``order`` / ``num_phases``: pinned (brute-force coverage and
     conflict-freeness, the phase counts and set sizes the paper states).
   * ``max_violation`` / ``objectives``: pinned by direct definition checks
@@ -44,7 +48,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     tmp = _LIB + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c99",
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c99", "-pthread",
            "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, _LIB)
@@ -86,6 +90,10 @@ def _load():
         lib.ora_sweep_l2.restype = i64
         lib.ora_objectives_l2.argtypes = [i64, dp, dp, dp, dp]
         lib.ora_objectives_l2.restype = None
+        lib.ora_sweep_threads.argtypes = [i64, i32, i64, dbl, dp, dp, dp, dp, dp, dp, i32, i64]
+        lib.ora_sweep_threads.restype = i64
+        lib.ora_sweep_l2_threads.argtypes = [i64, i32, i64, dp, dp, dp, i32, i64]
+        lib.ora_sweep_l2_threads.restype = i64
         _lib = lib
         return lib
 
@@ -158,6 +166,23 @@ class State:
         return int(_load().ora_sweep(self.n, schedule, tile, self.eps, _dp(self.d),
                                      _dp(self.winv), _dp(self.x), _dp(self.f),
                                      _dp(self.ytri), _dp(self.ypair), max_rows))
+
+    def sweep_threads(self, schedule: int = 1, tile: int = 16, threads: int = 0,
+                      max_phases: int = 0) -> int:
+        """The sweep with the units of each phase dealt to ``threads`` host
+        threads (0: all cores); with ``max_phases`` > 0 only the metric rows
+        of the first ``max_phases`` phases.  Returns the rows visited."""
+        t = threads if threads > 0 else (os.cpu_count() or 1)
+        if self.problem == "l2":
+            r = _load().ora_sweep_l2_threads(self.n, schedule, tile, _dp(self.winv), _dp(self.x),
+                                             _dp(self.ytri), t, max_phases)
+        else:
+            r = _load().ora_sweep_threads(self.n, schedule, tile, self.eps, _dp(self.d),
+                                          _dp(self.winv), _dp(self.x), _dp(self.f),
+                                          _dp(self.ytri), _dp(self.ypair), t, max_phases)
+        if r < 0:
+            raise RuntimeError("could not start the oracle's threads")
+        return int(r)
 
     def visit_triplet(self, i: int, j: int, k: int, rows: int = 3) -> None:
         _load().ora_visit_triplet(self.n, self.eps, _dp(self.winv), _dp(self.x),

@@ -1,6 +1,6 @@
 /*
  * Oracle: plain, serial, FP64 Dykstra's method for the regularized
- * correlation-clustering LP.  TEST INFRASTRUCTURE ONLY: only tests/,
+ * correlation-clustering LP (and a threaded form of the same sweep, below).  TEST INFRASTRUCTURE ONLY: only tests/,
  * __graft_entry__.smoke() and bench.py's CPU-baseline / reference legs may load
  * this code.  It shares nothing with the CUDA path.
  *
@@ -44,10 +44,20 @@
  *
  * Build with -ffp-contract=off: every product and sum is rounded on its own,
  * in the order written.
+ *
+ * Threaded sweeps (ora_sweep_threads, ora_sweep_l2_threads): the units of a
+ * phase (a set S_{i,k} in schedule 0, a first index i in schedule 1, a block
+ * triple in schedule 2) touch pairwise disjoint pairs and duals (Sec. III-A,
+ * III-C), so they are dealt round-robin to T threads that wait for each other
+ * at the end of every phase; every row is then computed from the same values
+ * as in the serial walk, and the result is the same bit for bit.
  */
+#define _POSIX_C_SOURCE 200809L
 #include <stdint.h>
 #include <stddef.h>
+#include <stdlib.h>
 #include <math.h>
+#include <pthread.h>
 
 static inline int64_t pidx(int64_t n, int64_t i, int64_t j) {
   return i * n - i * (i + 1) / 2 + (j - i - 1);
@@ -156,10 +166,30 @@ typedef struct {
   int64_t rec_cap;
   int64_t count;      /* triplets reached so far */
   int64_t phase;
+  /* threaded walks (all zero in a serial walk) */
+  int nthr, tid;      /* this thread visits the units u with u mod nthr == tid */
+  int64_t unit;       /* units started so far */
+  int skip;           /* the current unit belongs to another thread */
+  int64_t stop_after; /* > 0: stop after this many phases */
+  pthread_barrier_t* bar;
 } walk_t;
+
+/* Start of a unit of the current phase (units of one phase are disjoint). */
+static void unit_begin(walk_t* w) {
+  if (w->nthr > 1) w->skip = (w->unit % w->nthr) != w->tid;
+  w->unit++;
+}
+
+/* End of a phase: all threads wait here.  Returns 0 when the walk must stop. */
+static int end_phase(walk_t* w) {
+  w->phase++;
+  if (w->bar) pthread_barrier_wait(w->bar);
+  return !(w->stop_after > 0 && w->phase >= w->stop_after);
+}
 
 /* returns 0 when the walk must stop */
 static int walk_step(walk_t* w, int64_t i, int64_t j, int64_t k) {
+  if (w->skip) return 1;
   if (w->rec) {
     if (w->count < w->rec_cap) {
       int32_t* r = w->rec + 4 * w->count;
@@ -188,10 +218,11 @@ static int walk_sched0(walk_t* w) {
     for (c = 0; c <= g; ++c) {
       i = x + c;
       k = z - c;
+      unit_begin(w);
       for (j = i + 1; j <= k - 1; ++j)       /* the set S_{i,k} */
         if (!walk_step(w, i - 1, j - 1, k - 1)) return 0;
     }
-    w->phase++;
+    if (!end_phase(w)) return 0;
   }
   z = n;
   for (x = 2; x <= n - 2; ++x) {             /* second double loop */
@@ -199,10 +230,11 @@ static int walk_sched0(walk_t* w) {
     for (c = 0; c <= g; ++c) {
       i = x + c;
       k = z - c;
+      unit_begin(w);
       for (j = i + 1; j <= k - 1; ++j)
         if (!walk_step(w, i - 1, j - 1, k - 1)) return 0;
     }
-    w->phase++;
+    if (!end_phase(w)) return 0;
   }
   return 1;
 }
@@ -211,13 +243,15 @@ static int walk_sched0(walk_t* w) {
 static int walk_sched1(walk_t* w) {
   int64_t n = w->n;
   for (int64_t s = 0; s < n; ++s) {
-    for (int64_t i = 0; i < n; ++i)
+    for (int64_t i = 0; i < n; ++i) {
+      unit_begin(w);
       for (int64_t j = i + 1; j < n; ++j) {
         int64_t k = ((s - i - j) % n + n) % n;   /* the one k of this phase */
         if (k > j)
           if (!walk_step(w, i, j, k)) return 0;
       }
-    w->phase++;
+    }
+    if (!end_phase(w)) return 0;
   }
   return 1;
 }
@@ -231,6 +265,7 @@ static int walk_sched2(walk_t* w, int64_t B) {
       for (int64_t J = I; J < nb; ++J)
         for (int64_t K = J; K < nb; ++K) {
           if ((I + J + K) % nb != g) continue;
+          unit_begin(w);
           for (int64_t t = 0; t < B; ++t)
             for (int64_t a = 0; a < B; ++a)
               for (int64_t b = 0; b < B; ++b) {
@@ -240,7 +275,7 @@ static int walk_sched2(walk_t* w, int64_t B) {
                   if (!walk_step(w, i, j, k)) return 0;
               }
         }
-    w->phase++;
+    if (!end_phase(w)) return 0;
   }
   return 1;
 }
@@ -380,4 +415,108 @@ void ora_objectives_l2(int64_t n, const double* d, const double* w, const double
   out[2] = dd - 0.5 * sq;
   out[3] = 0.0;
   out[4] = 0.0;
+}
+
+/* ---- threaded sweeps ----------------------------------------------------
+ * The same sweep as ora_sweep / ora_sweep_l2, the units of each phase dealt
+ * to nthr threads (see the header).  With max_phases > 0 only the first
+ * max_phases phases of metric rows are visited (no pair rows), otherwise the
+ * whole sweep.  Returns the rows visited, or -1 when the threads could not be
+ * started (then nothing is visited). */
+
+typedef struct {
+  pthread_mutex_t mu;
+  pthread_cond_t cv;
+  int state;         /* 0: wait, 1: run, 2: give up */
+} start_gate;
+
+typedef struct {
+  walk_t w;
+  int sched;
+  int64_t B;
+  const double* d;   /* pair rows when pairs != 0 */
+  double *f, *ypair;
+  int pairs;
+  start_gate* gate;
+} thread_job;
+
+static void* thread_main(void* arg) {
+  thread_job* t = (thread_job*)arg;
+  pthread_mutex_lock(&t->gate->mu);            /* wait until every thread exists */
+  while (t->gate->state == 0) pthread_cond_wait(&t->gate->cv, &t->gate->mu);
+  int run = t->gate->state == 1;
+  pthread_mutex_unlock(&t->gate->mu);
+  if (!run) return NULL;
+  walk_schedule(&t->w, t->sched, t->B);
+  if (t->pairs) {                              /* every pair is its own unit */
+    int64_t P = ch2(t->w.n);
+    for (int64_t p = t->w.tid; p < P; p += t->w.nthr)
+      visit_pair(t->w.eps, t->d[p], t->w.winv[p], &t->w.x[p], &t->f[p], &t->ypair[2 * p], 2);
+  }
+  return NULL;
+}
+
+static int64_t sweep_threads(int64_t n, int sched, int64_t B, double eps, const double* d,
+                             const double* winv, double* x, double* f, double* ytri,
+                             double* ypair, int nthr, int64_t max_phases) {
+  if (nthr < 1) nthr = 1;
+  thread_job* jobs = (thread_job*)calloc((size_t)nthr, sizeof(thread_job));
+  pthread_t* ids = (pthread_t*)calloc((size_t)nthr, sizeof(pthread_t));
+  if (!jobs || !ids) {
+    free(jobs);
+    free(ids);
+    return -1;
+  }
+  pthread_barrier_t bar;
+  start_gate gate = {PTHREAD_MUTEX_INITIALIZER, PTHREAD_COND_INITIALIZER, 0};
+  if (pthread_barrier_init(&bar, NULL, (unsigned)nthr) != 0) {
+    free(jobs);
+    free(ids);
+    return -1;
+  }
+  for (int t = 0; t < nthr; ++t) {
+    walk_t w = {n, eps, winv, x, ytri, -1, NULL, 0, 0, 0};
+    w.nthr = nthr;
+    w.tid = t;
+    w.stop_after = max_phases > 0 ? max_phases : 0;
+    w.bar = &bar;
+    thread_job* j = &jobs[t];
+    j->w = w;
+    j->sched = sched;
+    j->B = B;
+    j->d = d;
+    j->f = f;
+    j->ypair = ypair;
+    j->pairs = d != NULL && max_phases <= 0;
+    j->gate = &gate;
+  }
+  int made = 1;                                /* thread 0 is this one */
+  while (made < nthr && pthread_create(&ids[made], NULL, thread_main, &jobs[made]) == 0) ++made;
+  pthread_mutex_lock(&gate.mu);
+  gate.state = made == nthr ? 1 : 2;
+  pthread_cond_broadcast(&gate.cv);
+  pthread_mutex_unlock(&gate.mu);
+  if (made == nthr) thread_main(&jobs[0]);
+  for (int t = 1; t < made; ++t) pthread_join(ids[t], NULL);
+  pthread_barrier_destroy(&bar);
+  int64_t rows = -1;
+  if (made == nthr) {
+    rows = 0;
+    for (int t = 0; t < nthr; ++t) rows += 3 * jobs[t].w.count;
+    if (d != NULL && max_phases <= 0) rows += 2 * ch2(n);
+  }
+  free(jobs);
+  free(ids);
+  return rows;
+}
+
+int64_t ora_sweep_threads(int64_t n, int sched, int64_t B, double eps, const double* d,
+                          const double* winv, double* x, double* f, double* ytri,
+                          double* ypair, int nthr, int64_t max_phases) {
+  return sweep_threads(n, sched, B, eps, d, winv, x, f, ytri, ypair, nthr, max_phases);
+}
+
+int64_t ora_sweep_l2_threads(int64_t n, int sched, int64_t B, const double* winv, double* x,
+                             double* ytri, int nthr, int64_t max_phases) {
+  return sweep_threads(n, sched, B, 1.0, NULL, winv, x, NULL, ytri, NULL, nthr, max_phases);
 }
