@@ -543,6 +543,23 @@ def _time_to_tol(args, n, d, w, stream, precision):
 
 # ---------------------------------------------------------------- oracle
 
+def host_cores(cpu_max="/sys/fs/cgroup/cpu.max"):
+    """Host cores this process may use: the CPU affinity set, capped by a
+    cgroup v2 CPU quota when one is set."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        n = os.cpu_count() or 1
+    try:
+        with open(cpu_max) as fh:
+            quota, period = fh.read().split()[:2]
+        if quota != "max":
+            n = min(n, max(1, -(-int(quota) // int(period))))
+    except (OSError, ValueError):
+        pass
+    return max(1, n)
+
+
 def cpu_baseline(workload_name):
     """Time the oracle as it stands on one sweep of the workload: its
     threaded form on every host core (the units of each phase dealt to the
@@ -551,7 +568,7 @@ def cpu_baseline(workload_name):
     from instances import workload
     n, d, w, desc = workload(workload_name)
     T = n * (n - 1) * (n - 2) // 6
-    cores = os.cpu_count() or 1
+    cores = host_cores()
     st = oracle.State(n, d, w, 0.2)
     t = time.perf_counter()
     st.sweep_threads(2, 16, cores)
@@ -577,7 +594,7 @@ def run_reference(args, rank):
     from instances import workload
     n, d, w, desc = workload(args.workload)
     T = n * (n - 1) * (n - 2) // 6
-    cores = os.cpu_count() or 1
+    cores = host_cores()
     phases = oracle.num_phases(n, 2, args.tile)
     st = oracle.State(n, d, w, 0.2)
     t = time.perf_counter()

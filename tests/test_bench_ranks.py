@@ -65,3 +65,17 @@ def test_reference_arm_runs_on_rank_zero_only():
     assert bench.run_reference(Args(), 1) is None
     out = bench.run_reference(Args(), 0)
     assert out["impl"] == "reference" and out["value"] > 0
+
+
+def test_host_cores_reads_the_cgroup_quota(tmp_path):
+    sys.path.insert(0, ROOT)
+    import bench
+    f = tmp_path / "cpu.max"
+    free = bench.host_cores(str(tmp_path / "absent"))
+    assert free >= 1
+    f.write_text("max 100000\n")
+    assert bench.host_cores(str(f)) == free
+    f.write_text("150000 100000\n")
+    assert bench.host_cores(str(f)) == min(free, 2)
+    f.write_text("50000 100000\n")
+    assert bench.host_cores(str(f)) == 1
