@@ -200,6 +200,17 @@ int cc_create_device(cc_handle** out, int64_t n, const double* d_dev, const doub
  * time-out inside a sweep is reported by the next synchronizing call. */
 int cc_sweep(cc_handle* h, int64_t k);
 
+/* `passes` >= 0 visits of every pair's two rows (x - f <= d, then
+ * d - x <= f) and of no metric row: Algorithm 1's row step on the pair
+ * block only, i.e. Hildreth's coordinate ascent on the pair duals with the
+ * triangle duals held (Sec. II-B).  Pairs share no variable, so this equals
+ * `passes` pair-only sweeps.  Useful after setting triangle duals without
+ * pair duals: it moves the pair duals to their best values for the given
+ * triangle duals.  The sweep count is unchanged.  Tiled schedule (any form,
+ * precision and store; CC_ERR_UNSUPPORTED otherwise); a no-op for l2
+ * nearness, which has no pair rows.  Asynchronous on the handle's stream. */
+int cc_pair_passes(cc_handle* h, int32_t passes);
+
 /* Convergence quantities at the current state (synchronizes). */
 int cc_check(cc_handle* h, cc_stats* st);
 
@@ -345,22 +356,25 @@ const char* cc_batch_last_error(const cc_batch* b);
  *   Candidates: triplets (i, j, k) with at least one edge (d = 0) among
  *     their three pairs; all other triangle duals and all pair duals start
  *     at 0.
- *   Features (5 floats, row stride CC_WS_FEAT): d_ij, d_ik, d_jk,
- *     log(1 + (deg i + deg j + deg k) / mean degree),
- *     log(1 + number of objects adjacent to all three); degrees count edges.
- *   Network: 5 -> 64 -> 64 -> 3, ReLU, softplus output = the triplet's three
+ *   Features (10 floats, row stride CC_WS_FEAT): d_ij, d_ik, d_jk,
+ *     log(1 + deg u / mean degree) for u = i, j, k,
+ *     log(1 + common neighbours) of ij, ik, jk and of all three; edges are
+ *     the pairs with d = 0.
+ *   Network: 10 -> 64 -> 64 -> 3, ReLU, softplus output = the triplet's three
  *     duals y; BF16 weights and activations, FP32 accumulation, on the
  *     tensor cores (mma.sync m16n8k16).
- *   Parameters: CC_WS_NPARAM floats, W1[5][64], b1[64], W2[64][64], b2[64],
+ *   Parameters: CC_WS_NPARAM floats, W1[10][64], b1[64], W2[64][64], b2[64],
  *     W3[64][3], b3[3] (row-major [in][out]; y = x W + b).
  * Rows of the three outputs follow the handle's internal triplet order; a
  * network is trained on samples of that same order (cc_ws_samples). */
-#define CC_WS_NPARAM 4739
-#define CC_WS_FEAT 8
+#define CC_WS_NPARAM 5059
+#define CC_WS_FEAT 12
+#define CC_WS_PAIR_PASSES 16
 
 /* Replace the handle's duals by the network's prediction (host params),
  * outputs below `threshold` set to 0, pair duals 0, rebuild x and f from
- * them in FP64 and reset the sweep count.  *candidates (nullable): the
+ * them in FP64, run CC_WS_PAIR_PASSES pair passes (cc_pair_passes: the pair
+ * duals settle to the predicted triangle duals) and reset the sweep count.  *candidates (nullable): the
  * number of candidate triplets.  Needs the tiled schedule, fused form and an
  * FP64 state (CC_ERR_UNSUPPORTED otherwise).  Synchronous.  Errors:
  * CC_ERR_ARG, CC_ERR_UNSUPPORTED, CC_ERR_OOM, CC_ERR_CUDA. */

@@ -129,6 +129,10 @@ class Solver:
     def sweep(self, k: int = 1) -> None:
         cc_sweep(self.h, k)
 
+    def pair_passes(self, passes: int) -> None:
+        """Visit the pair rows alone `passes` times (see cc_pair_passes)."""
+        _native.cc_pair_passes(self.h, passes)
+
     def check(self) -> dict:
         return cc_check(self.h).as_dict()
 

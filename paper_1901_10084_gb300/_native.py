@@ -92,10 +92,11 @@ EXPORTS = ("cc_opts_default", "cc_create", "cc_create_device", "cc_sweep", "cc_c
            "cc_refine_fp64", "cc_set_duals", "cc_get_trace", "cc_batch_create", "cc_batch_size",
            "cc_batch_handle", "cc_batch_sweep", "cc_batch_solve", "cc_batch_autotune", "cc_batch_destroy",
            "cc_batch_last_error", "cc_warm_start_mlp", "cc_ws_samples", "cc_mlp_forward", "cc_mlp_grad",
-           "cc_mlp_train")
+           "cc_mlp_train", "cc_pair_passes")
 
-CC_WS_NPARAM = 4739
-CC_WS_FEAT = 8
+CC_WS_NPARAM = 5059
+CC_WS_FEAT = 12
+CC_WS_PAIR_PASSES = 16
 
 _lib = None
 _lock = threading.Lock()
@@ -131,6 +132,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         lib.cc_create_device.restype = ctypes.c_int
         lib.cc_sweep.argtypes = [H, i64]
         lib.cc_sweep.restype = ctypes.c_int
+        lib.cc_pair_passes.argtypes = [H, ctypes.c_int32]
+        lib.cc_pair_passes.restype = ctypes.c_int
         lib.cc_check.argtypes = [H, ctypes.POINTER(cc_stats)]
         lib.cc_check.restype = ctypes.c_int
         lib.cc_solve.argtypes = [H, ctypes.c_double, i64, ctypes.POINTER(ctypes.c_int64)]
@@ -236,6 +239,10 @@ def cc_create_device(n: int, d_ptr: int, w_ptr: int, opts: cc_opts | None = None
 
 def cc_sweep(h, k: int) -> None:
     _check(load().cc_sweep(h, k), h)
+
+
+def cc_pair_passes(h, passes: int) -> None:
+    _check(load().cc_pair_passes(h, passes), h)
 
 
 def cc_check(h) -> cc_stats:

@@ -991,6 +991,35 @@ int cc_create(cc_handle** out, int64_t n, const double* d, const double* w, cons
   return CC_OK;
 }
 
+int cc_pair_passes(cc_handle* h, int32_t passes) {
+  if (!h) return fail(nullptr, CC_ERR_ARG, "handle is NULL");
+  if (passes < 0) return fail(h, CC_ERR_ARG, "passes must be >= 0");
+  if (h->o.schedule != CC_SCHED_TILED) return fail(h, CC_ERR_UNSUPPORTED, "pair passes need the tiled schedule");
+  if (h->o.problem == CC_PROB_L2 || passes == 0) return CC_OK;   // l2 nearness has no pair rows
+  CK(h, cudaSetDevice(h->dev));
+  const int grid = grid_for(h, (int64_t)h->ntiles * h->B * h->B, 256);
+  if (h->fp32) {
+    TiledArgs<float> a = tiled_args<float>(h);
+    if (h->B == 8) k_pair_passes<float, false, 8><<<grid, 256, 0, h->st>>>(a, passes);
+    else if (h->B == 16) k_pair_passes<float, false, 16><<<grid, 256, 0, h->st>>>(a, passes);
+    else k_pair_passes<float, false, 32><<<grid, 256, 0, h->st>>>(a, passes);
+  } else {
+    TiledArgs<double> a = tiled_args<double>(h);
+    if (h->o.exact) {
+      if (h->B == 8) k_pair_passes<double, true, 8><<<grid, 256, 0, h->st>>>(a, passes);
+      else if (h->B == 16) k_pair_passes<double, true, 16><<<grid, 256, 0, h->st>>>(a, passes);
+      else k_pair_passes<double, true, 32><<<grid, 256, 0, h->st>>>(a, passes);
+    } else {
+      if (h->B == 8) k_pair_passes<double, false, 8><<<grid, 256, 0, h->st>>>(a, passes);
+      else if (h->B == 16) k_pair_passes<double, false, 16><<<grid, 256, 0, h->st>>>(a, passes);
+      else k_pair_passes<double, false, 32><<<grid, 256, 0, h->st>>>(a, passes);
+    }
+  }
+  CK(h, cudaGetLastError());
+  h->fresh = false;
+  return CC_OK;
+}
+
 int cc_sweep(cc_handle* h, int64_t k) {
   if (!h) return fail(nullptr, CC_ERR_ARG, "handle is NULL");
   if (k < 0) return fail(h, CC_ERR_ARG, "k must be >= 0");
@@ -1823,6 +1852,7 @@ int cc_warm_start_mlp(cc_handle* h, const float* params, double threshold, int64
   else k_rebuild_mask<double, 32><<<g2, 256, 0, h->st>>>((const double*)h->zt, h->mask, h->mask_words);
   CK(h, cudaGetLastError());
   rc = resync_fp64(h);
+  if (rc == CC_OK) rc = cc_pair_passes(h, CC_WS_PAIR_PASSES);
   CK(h, cudaStreamSynchronize(h->st));
   dfree(h, pd);
   ws_release(h, c);

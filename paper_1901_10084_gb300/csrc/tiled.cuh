@@ -984,6 +984,32 @@ __device__ __forceinline__ void flow_pair_tile(const TiledArgs<T>& a, int tl) {
   }
 }
 
+// `passes` visits of every pair's two rows and nothing else (Hildreth's
+// coordinate ascent restricted to the pair block of the dual, Sec. II-B).
+// The pair rows of different pairs share no variable, so the passes of one
+// pair run in registers one after the other, which is the same as `passes`
+// pair-only sweeps one after the other.
+template <typename T, bool EXACT, int B>
+__global__ void k_pair_passes(TiledArgs<T> a, int passes) {
+  using C = TileCfg<B>;
+  const int64_t total = (int64_t)a.ntiles * C::BB;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int tl = (int)(e / C::BB), slot = (int)(e % C::BB);
+    const int pk = a.tile_list[tl];
+    const int I = pk & 0xffff, J = pk >> 16;
+    const int la = slot / B, lb = slot % B;
+    if (!((I < J || la < lb) && J * B + lb < a.n)) continue;
+    T* zq = a.zp + (int64_t)tl * (2 * C::BB) + slot;
+    T x = a.x[e], f = a.f[e], zp = zq[0], zm = zq[C::BB];
+    const T d = a.d[e], wv = a.winv[e];
+    for (int k = 0; k < passes; ++k) pair_rows<T, EXACT>(x, f, d, wv, a.eps, zp, zm);
+    a.x[e] = x;
+    a.f[e] = f;
+    zq[0] = zp;
+    zq[C::BB] = zm;
+  }
+}
+
 // One sweep as a dataflow over tiles.  Work items, taken in order from one
 // counter: the block triples in schedule order (phase-major, largest first
 // inside a phase), then one pair item per tile.  Every phase visits every

@@ -1,5 +1,5 @@
 // Learned dual warm start (not in the paper).  A small MLP predicts the three
-// triangle duals of a triplet from five features; the predicted duals are
+// triangle duals of a triplet from ten features; the predicted duals are
 // written into the dual store and x, f are rebuilt from them through the
 // identity v = v0 - W^{-1} A^T y / eps that Dykstra's method keeps, so the
 // solve continues from a consistent state and converges to the same optimum
@@ -8,20 +8,23 @@
 //
 // Candidates: triplets with at least one edge (d = 0) among their three
 // pairs; every other triplet keeps dual 0 (three non-edges give rows with a
-// slack near 1).  Features of a candidate (a, b, c), internal labels a<b<c:
-//   d_ab, d_ac, d_bc; log(1 + (deg a + deg b + deg c) / mean degree);
-//   log(1 + the number of objects adjacent to all three) (degrees from d = 0).
-// Network: 5 -> 64 -> 64 -> 3, ReLU, softplus output, BF16 weights and
+// slack near 1).  Features of a candidate (a, b, c), internal labels a<b<c,
+// edges from d = 0:
+//   d_ab, d_ac, d_bc; log(1 + deg u / mean degree) for u = a, b, c;
+//   log(1 + common neighbours) of ab, ac, bc and of all three.
+// Network: 10 -> 64 -> 64 -> 3, ReLU, softplus output, BF16 weights and
 // activations, FP32 accumulation (mma.sync m16n8k16 on the tensor cores).
+// After the rebuild, a few passes over the pair rows alone let the pair
+// duals (not predicted, started at 0) settle to the predicted triangle duals.
 #pragma once
 
 namespace ccd {
 
-constexpr int WS_IN = 5, WS_H = 64, WS_OUT = 3;
-// parameter layout (floats): W1[5][64], b1[64], W2[64][64], b2[64], W3[64][3], b3[3]
+constexpr int WS_IN = 10, WS_H = 64, WS_OUT = 3;
+// parameter layout (floats): W1[10][64], b1[64], W2[64][64], b2[64], W3[64][3], b3[3]
 constexpr int WS_W1 = 0, WS_B1 = WS_W1 + WS_IN * WS_H, WS_W2 = WS_B1 + WS_H, WS_B2 = WS_W2 + WS_H * WS_H,
               WS_W3 = WS_B2 + WS_H, WS_B3 = WS_W3 + WS_H * WS_OUT, WS_NPARAM = WS_B3 + WS_OUT;
-constexpr int WS_FEAT = 8;  // feature row stride (5 used)
+constexpr int WS_FEAT = 12;  // feature row stride (10 used)
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat16 l = __float2bfloat16_rn(lo), h = __float2bfloat16_rn(hi);
@@ -211,16 +214,27 @@ __global__ void k_ws_features(const int64_t* __restrict__ cand, int64_t count, c
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t pk = cand[q];
     const int a = (int)(pk & 0x1fffff), b = (int)((pk >> 21) & 0x1fffff), c = (int)(pk >> 42);
-    int common = 0;
-    for (int w = 0; w < words; ++w)
-      common += __popc(adj[(int64_t)a * words + w] & adj[(int64_t)b * words + w] & adj[(int64_t)c * words + w]);
+    int cab = 0, cac = 0, cbc = 0, c3 = 0;   // common neighbours of each pair and of all three
+    for (int w = 0; w < words; ++w) {
+      const uint32_t na = adj[(int64_t)a * words + w], nb_ = adj[(int64_t)b * words + w],
+                     nc = adj[(int64_t)c * words + w];
+      cab += __popc(na & nb_);
+      cac += __popc(na & nc);
+      cbc += __popc(nb_ & nc);
+      c3 += __popc(na & nb_ & nc);
+    }
     float* f = feat + q * WS_FEAT;
     f[0] = (float)d[tiled_offset(nb, B, a, b)];
     f[1] = (float)d[tiled_offset(nb, B, a, c)];
     f[2] = (float)d[tiled_offset(nb, B, b, c)];
-    f[3] = log1pf((float)(deg[a] + deg[b] + deg[c]) * inv_mean_deg);
-    f[4] = log1pf((float)common);
-    f[5] = f[6] = f[7] = 0.f;
+    f[3] = log1pf((float)deg[a] * inv_mean_deg);
+    f[4] = log1pf((float)deg[b] * inv_mean_deg);
+    f[5] = log1pf((float)deg[c] * inv_mean_deg);
+    f[6] = log1pf((float)cab);
+    f[7] = log1pf((float)cac);
+    f[8] = log1pf((float)cbc);
+    f[9] = log1pf((float)c3);
+    f[10] = f[11] = 0.f;
   }
 }
 

@@ -5,7 +5,7 @@ cc_warm_start_mlp.
 The method being warm-started is Dykstra's (Hildreth's) projection method of
 Sec. II-B (Algorithm 1): coordinate ascent on the dual of Eq. (qp), which
 reaches the same optimum from any nonnegative dual start once the primal
-iterate is rebuilt from the duals.  A network 5 -> 64 -> 64 -> 3 maps
+iterate is rebuilt from the duals.  A network 10 -> 64 -> 64 -> 3 maps
 features of a triplet with at least one edge to its three duals; its
 forward and backward passes and the Adam steps run in the library's
 tensor-core kernels.  Device buffers come from PyTorch (plumbing only).
@@ -18,7 +18,7 @@ import torch
 from . import _native
 from ._native import CC_WS_FEAT, CC_WS_NPARAM
 
-N_IN, N_H, N_OUT = 5, 64, 3
+N_IN, N_H, N_OUT = 10, 64, 3
 
 
 def unpack(params):

@@ -78,6 +78,7 @@ def test_warm_start_calls_reject_null_arguments(lib):
     assert lib.cc_warm_start_mlp(None, pp, 0.0, None) == N.CC_ERR_ARG
     assert lib.cc_ws_samples(None, None, None, 0, None) == N.CC_ERR_ARG
     assert lib.cc_mlp_forward(None, None, None, 4, None) == N.CC_ERR_ARG
+    assert lib.cc_pair_passes(None, 1) == N.CC_ERR_ARG
     assert lib.cc_mlp_forward(pp, None, None, -1, None) == N.CC_ERR_ARG
     assert lib.cc_mlp_grad(pp, None, None, 16, 1.0, pp, None, None) == N.CC_ERR_ARG
     assert lib.cc_mlp_train(pp, None, None, 16, 16, 1, 1e-3, 0, 1.0, None, None) == N.CC_ERR_ARG
@@ -92,14 +93,15 @@ def test_warm_start_calls_reject_null_arguments(lib):
 def test_warm_start_parameter_count_matches_the_network():
     from paper_1901_10084_gb300 import _native as N
     from paper_1901_10084_gb300 import warmstart
-    assert N.CC_WS_NPARAM == 5 * 64 + 64 + 64 * 64 + 64 + 64 * 3 + 3
+    assert N.CC_WS_NPARAM == 10 * 64 + 64 + 64 * 64 + 64 + 64 * 3 + 3
     src = open(os.path.join(ROOT, "include", "ccdyk.h")).read()
     assert re.search(r"#define CC_WS_NPARAM %d\b" % N.CC_WS_NPARAM, src)
     assert re.search(r"#define CC_WS_FEAT %d\b" % N.CC_WS_FEAT, src)
+    assert re.search(r"#define CC_WS_PAIR_PASSES %d\b" % N.CC_WS_PAIR_PASSES, src)
     p = warmstart.init_params(0)
     assert p.shape == (N.CC_WS_NPARAM,) and p.dtype.name == "float32"
     W1, b1, W2, b2, W3, b3 = warmstart.unpack(p)
-    assert W1.shape == (5, 64) and W2.shape == (64, 64) and W3.shape == (64, 3) and b3.shape == (3,)
+    assert W1.shape == (10, 64) and W2.shape == (64, 64) and W3.shape == (64, 3) and b3.shape == (3,)
 
 
 def test_checked_library_exports_the_same_symbols(lib):

@@ -34,7 +34,7 @@ def _reference_forward(params, feat):
     torch = _torch()
     from paper_1901_10084_gb300.warmstart import unpack
     W1, b1, W2, b2, W3, b3 = [torch.tensor(a) for a in unpack(params)]
-    x = _bf(feat[:, :5])
+    x = _bf(feat[:, :10])
     h1 = x @ _bf(W1) + b1
     h2 = _bf(torch.relu(h1)) @ _bf(W2) + b2
     o = _bf(torch.relu(h2)) @ _bf(W3) + b3
@@ -54,11 +54,12 @@ def _features_numpy(n, d):
     for a, b in zip(iu, ju):
         for c in range(b + 1, n):
             if A[a, b] or A[a, c] or A[b, c]:
+                cn = [int(np.sum(A[u] & A[v])) for u, v in ((a, b), (a, c), (b, c))]
                 common = int(np.sum(A[a] & A[b] & A[c]))
-                rows.append([D[a, b], D[a, c], D[b, c], np.log1p((deg[a] + deg[b] + deg[c]) / mean),
-                             np.log1p(common)])
+                rows.append([D[a, b], D[a, c], D[b, c], np.log1p(deg[a] / mean), np.log1p(deg[b] / mean),
+                             np.log1p(deg[c] / mean), *np.log1p(cn), np.log1p(common)])
                 trip.append((a, b, c))
-    return np.array(rows, dtype=np.float64).reshape(-1, 5), trip
+    return np.array(rows, dtype=np.float64).reshape(-1, 10), trip
 
 
 @pytest.mark.parametrize("n,tile", [(60, 16), (75, 8)])
@@ -73,8 +74,8 @@ def test_features_and_targets_match_a_numpy_recount(n, tile):
     feat = feat.cpu().numpy()
     targ = targ.cpu().numpy()
     assert feat.shape[0] == len(trip)
-    np.testing.assert_allclose(feat[:, :5], ref, rtol=1e-6, atol=1e-6)
-    assert np.all(feat[:, 5:] == 0)
+    np.testing.assert_allclose(feat[:, :10], ref, rtol=1e-6, atol=1e-6)
+    assert np.all(feat[:, 10:] == 0)
     idx = np.array([oracle.trank(n, a, b, c) for a, b, c in trip])
     expect = yt.reshape(-1, 3)[idx]
     np.testing.assert_allclose(targ, expect, rtol=1e-6, atol=1e-30)
@@ -82,10 +83,10 @@ def test_features_and_targets_match_a_numpy_recount(n, tile):
 
 def _sample_features(count, seed):
     rng = np.random.default_rng(seed)
-    f = np.zeros((count, 8), dtype=np.float32)
+    f = np.zeros((count, 12), dtype=np.float32)
     f[:, :3] = rng.integers(0, 2, (count, 3))
-    f[:, 3] = rng.uniform(0.3, 3.0, count)
-    f[:, 4] = rng.uniform(0.0, 3.0, count)
+    f[:, 3:6] = rng.uniform(0.1, 2.5, (count, 3))
+    f[:, 6:10] = rng.uniform(0.0, 3.0, (count, 4))
     return f
 
 
@@ -103,7 +104,7 @@ def test_forward_matches_fp32_reference(count):
 def test_forward_of_empty_input():
     torch = _torch()
     from paper_1901_10084_gb300 import warmstart
-    out = warmstart.forward(warmstart.init_params(0), torch.zeros((0, 8), device="cuda"))
+    out = warmstart.forward(warmstart.init_params(0), torch.zeros((0, 12), device="cuda"))
     assert out.shape == (0, 3)
 
 
@@ -121,12 +122,12 @@ def test_gradient_matches_fp32_autograd(count, pos_weight):
     g, loss = warmstart.grad(params, feat.cuda(), target.cuda(), pos_weight=pos_weight)
     p = torch.tensor(params, requires_grad=True)
     parts, o = [], 0
-    for size in (5 * 64, 64, 64 * 64, 64, 64 * 3, 3):
+    for size in (10 * 64, 64, 64 * 64, 64, 64 * 3, 3):
         parts.append(p[o:o + size])
         o += size
-    W1, b1, W2, b2, W3, b3 = (parts[0].view(5, 64), parts[1], parts[2].view(64, 64), parts[3],
+    W1, b1, W2, b2, W3, b3 = (parts[0].view(10, 64), parts[1], parts[2].view(64, 64), parts[3],
                               parts[4].view(64, 3), parts[5])
-    x = _bf(feat[:, :5])
+    x = _bf(feat[:, :10])
     h1 = x @ W1 + b1
     h2 = torch.relu(h1) @ W2 + b2
     out = torch.nn.functional.softplus(torch.relu(h2) @ W3 + b3)
@@ -136,7 +137,7 @@ def test_gradient_matches_fp32_autograd(count, pos_weight):
     gref = p.grad.numpy()
     assert abs(loss - ref_loss.item()) <= 2e-2 * ref_loss.item()
     o = 0
-    for size in (5 * 64, 64, 64 * 64, 64, 64 * 3, 3):
+    for size in (10 * 64, 64, 64 * 64, 64, 64 * 3, 3):
         a, b = g[o:o + size], gref[o:o + size]
         assert np.linalg.norm(a - b) <= 5e-2 * np.linalg.norm(b) + 1e-7, (o, size)
         o += size
@@ -176,7 +177,7 @@ def test_warm_started_solve_reaches_the_cold_optimum(interleave):
                 cand = s.warm_start(params, threshold=1e-3)
                 assert cand > 0
                 yt, yp = s.get_duals()
-                assert yt.min() >= 0.0 and np.all(yp == 0.0)
+                assert yt.min() >= 0.0 and yp.min() >= 0.0   # pair duals from the pair passes
                 x, f = s.get_x()
                 from oracle.dense import invariant_residual
                 assert invariant_residual(n, d, w, 0.2, x, f, yt, yp) <= 1e-12
@@ -188,22 +189,28 @@ def test_warm_started_solve_reaches_the_cold_optimum(interleave):
     assert np.max(np.abs(x1 - x0)) <= 1e-4
 
 
-def test_zero_prediction_is_the_cold_start_bitwise():
-    """Threshold above every output: all duals 0, so the rebuilt state is
-    x0 and the following sweeps match a fresh solver bit for bit."""
-    from paper_1901_10084_gb300 import warmstart
+def test_zero_prediction_is_the_cold_start_plus_pair_passes_bitwise():
+    """Threshold above every output: all triangle duals 0, so the rebuilt
+    state is x0 and the warm start ends with CC_WS_PAIR_PASSES pair passes
+    from it; that state and the following sweeps match a fresh solver given
+    the same pair passes, bit for bit."""
+    from paper_1901_10084_gb300 import _native, warmstart
     n = 90
     d, w, _ = chung_lu(n, 2.5, 8.0, seed=9, weights=(0.5, 2.0))
     params = warmstart.init_params(1)
     with _solver(n, d, w, tile=16) as a, _solver(n, d, w, tile=16) as b:
         a.sweep(4)
         a.warm_start(params, threshold=1e30)
-        a.sweep(3)
-        b.sweep(3)
-        xa, fa = a.get_x()
-        xb, fb = b.get_x()
-        assert np.array_equal(xa, xb) and np.array_equal(fa, fb)
-        assert a.stats()["sweeps"] == 3
+        b.pair_passes(_native.CC_WS_PAIR_PASSES)
+        for _ in range(2):
+            xa, fa = a.get_x()
+            xb, fb = b.get_x()
+            assert np.array_equal(xa, xb) and np.array_equal(fa, fb)
+            for u, v in zip(a.get_duals(), b.get_duals()):
+                assert np.array_equal(u, v)
+            a.sweep(3)
+            b.sweep(3)
+        assert a.stats()["sweeps"] == 6
 
 
 def test_warm_start_rejects_the_exact_form():
