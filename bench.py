@@ -344,8 +344,8 @@ def _warm_start(args, stream):
     instances (exponent 2.5, mean degree 8, seeds 400000+i) to the tolerance
     as batches, train the network on their duals, then solve Chung-Lu
     n=1000 (seed 1) and n=2000 (seed 4) from the cold start and from the
-    predicted duals.  Warm wall time includes features, inference and the
-    resync."""
+    predicted duals.  Warm wall time includes features, inference, the
+    resync and the pair passes."""
     import numpy as np
     import torch
 
@@ -385,6 +385,8 @@ def _warm_start(args, stream):
                 r[mode] = {"seconds": time.perf_counter() - t, "sweeps": k, "converged": ok,
                            "lp_objective": s.check()["lp_objective"]}
         r["speedup"] = r["cold"]["seconds"] / r["warm"]["seconds"]
+        r["lp_objective_rel_vs_cold"] = (abs(r["warm"]["lp_objective"] - r["cold"]["lp_objective"])
+                                         / abs(r["cold"]["lp_objective"]))
         rec[name] = r
     return rec
 
