@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--no-precision-form", action="store_true",
                    help="skip the FP32 bulk + FP64 refinement time-to-tolerance solve")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
+    p.add_argument("--no-chain", action="store_true", help="skip the dependency-chain analysis of a traced sweep")
     p.add_argument("--batch-count", type=int, default=256)
     p.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start measurement")
     p.add_argument("--no-l2", action="store_true", help="skip the l2 metric nearness measurement")
@@ -275,6 +276,8 @@ def run_ours(args, rank, world, local_rank):
                               "lp_objective_rel": abs(r32["lp_objective"] - r64["lp_objective"])
                               / abs(r64["lp_objective"])}
             out["precision_form"] = pf
+    if rank == 0 and not args.no_chain and args.schedule == "tiled":
+        out["chain"] = _chain(args, n, d, w, stream)
     if rank == 0 and not args.no_batch and args.schedule == "tiled":
         out["batched_form"] = _batched(args, stream)
     if rank == 0 and not args.no_warm_start and args.schedule == "tiled":
@@ -287,6 +290,31 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
         dist.destroy_process_group()
     return out
+
+
+def _chain(args, n, d, w, stream):
+    """The sweep against its dependency-chain bound: a traced solver (per-item
+    timestamps on the GPU clock) on the bench workload; after 3 and after 60
+    sweeps, the span of one traced sweep, its longest chain of dependent
+    block triples (one per phase) and that chain's own work.  chain_frac =
+    chain work / span: the part of the sweep that no number of CTAs could
+    remove; the rest is the hand-off between the chain's items (release,
+    visibility, staging of the next item)."""
+    import torch
+
+    import paper_1901_10084_gb300 as cc
+    from paper_1901_10084_gb300 import chain
+    rec = {"note": "traced sweeps (timestamps add a little time); work of an item = release - dependencies met"}
+    with cc.Solver(n, d, w, eps=0.2, tile=args.tile, stream=stream, trace=True) as s:
+        done = 0
+        for k in (3, 60):
+            s.sweep(k - done)
+            done = k
+            torch.cuda.synchronize()
+            r = chain.critical_path(s.trace(), n, args.tile)
+            r.pop("chain")
+            rec[f"after_{k}_sweeps"] = r
+    return rec
 
 
 def _batched(args, stream):
