@@ -112,3 +112,27 @@ def critical_path(trace: np.ndarray, n: int, B: int) -> dict:
             "item_work_mean_us": float(work[:nbt].mean()) / 1e3,
             "chain_item_work_mean_us": float(work[chain].mean()) / 1e3,
             "started_early": early, "chain": chain}
+
+
+def simulate(trace: np.ndarray, n: int, B: int, slots=None, hop_ns: float = 1000.0) -> float:
+    """Span (us) of a model sweep with the traced work of each item: `slots`
+    CTAs (None: one per item) take the items in list order, an item starts
+    when it is taken and `hop_ns` after its last predecessor's release, and
+    holds its CTA for its work.  With unlimited slots this is the longest
+    chain with a fixed hand-off per hop."""
+    import heapq
+    tr = np.asarray(trace, dtype=np.int64)
+    deps, nbt = dependencies(n, B)
+    if tr.shape[0] != len(deps):
+        raise ValueError(f"trace has {tr.shape[0]} items, the schedule {len(deps)}")
+    work = np.zeros(len(deps))
+    work[:nbt] = np.maximum(tr[:nbt, 3] - tr[:nbt, 1], 0)
+    free = [0.0] * (len(deps) if slots is None else int(slots))
+    heapq.heapify(free)
+    rel = np.zeros(len(deps))
+    for w in range(len(deps)):
+        taken = heapq.heappop(free)
+        start = max([taken] + [rel[p] + hop_ns for p in deps[w]])
+        rel[w] = start + work[w]
+        heapq.heappush(free, rel[w])
+    return float(rel.max()) / 1e3

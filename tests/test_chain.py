@@ -99,3 +99,27 @@ def test_trace_of_another_size_is_refused():
     tr, *_ = _synthetic_trace(40, 8, 5)
     with pytest.raises(ValueError):
         chain.critical_path(tr, 41, 8)
+
+
+@pytest.mark.parametrize("n,B,hop", [(40, 8, 0.0), (50, 16, 700.0)])
+def test_model_with_unlimited_slots_is_the_longest_chain(n, B, hop):
+    tr, work, deps, nbt = _synthetic_trace(n, B, 6)
+    g = nx.DiGraph()
+    for w in range(len(deps)):
+        ww = int(work[w]) if w < nbt else 0
+        g.add_edge("s", w, weight=ww)
+        for p in deps[w]:
+            g.add_edge(p, w, weight=ww + hop)
+    best = nx.dag_longest_path_length(g, weight="weight")
+    assert chain.simulate(tr, n, B, None, hop) * 1e3 == pytest.approx(best)
+
+
+def test_model_with_one_slot_runs_the_items_one_after_another():
+    n, B, hop = 40, 8, 500.0
+    tr, work, deps, nbt = _synthetic_trace(n, B, 7)
+    t, rel = 0.0, {}
+    for w in range(len(deps)):
+        t = max([t] + [rel[p] + hop for p in deps[w]]) + (work[w] if w < nbt else 0)
+        rel[w] = t
+    assert chain.simulate(tr, n, B, 1, hop) * 1e3 == pytest.approx(t)
+    assert chain.simulate(tr, n, B, 1, hop) >= chain.simulate(tr, n, B, 4, hop) >= chain.simulate(tr, n, B, None, hop)
