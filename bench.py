@@ -415,6 +415,18 @@ def _warm_start(args, stream):
         r["speedup"] = r["cold"]["seconds"] / r["warm"]["seconds"]
         r["lp_objective_rel_vs_cold"] = (abs(r["warm"]["lp_objective"] - r["cold"]["lp_objective"])
                                          / abs(r["cold"]["lp_objective"]))
+        # the FP32 bulk form, cold and warm-started (the warm start runs in FP64 and is rounded)
+        for mode in ("cold_fp32", "warm_fp32"):
+            with cc.Solver(n, d, w, tile=args.tile, check_every=5, stream=stream, precision="fp32_refine") as s:
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                if mode == "warm_fp32":
+                    s.warm_start(params, args.ws_threshold)
+                ok, k = s.solve(args.tol, args.ttt_max_sweeps)
+                torch.cuda.synchronize()
+                r[mode] = {"seconds": time.perf_counter() - t, "sweeps": k, "converged": ok,
+                           "fp32_sweeps": s.stats()["fp32_sweeps"], "lp_objective": s.check()["lp_objective"]}
+        r["speedup_warm_fp32_vs_cold_fp64"] = r["cold"]["seconds"] / r["warm_fp32"]["seconds"]
         rec[name] = r
     return rec
 

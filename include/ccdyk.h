@@ -113,8 +113,10 @@ typedef struct cc_opts {
                                row updated: the reference the filtered forms
                                equal in value).  All give the same values. */
   double refine_at;         /* CC_PREC_FP32_REFINE: cc_solve leaves FP32 when
-                               the violation is <= max(tol, refine_at) or stops
-                               decreasing between checks; default 1e-5 */
+                               the violation is <= a = max(tol, refine_at),
+                               or is <= 100 a and stops decreasing between
+                               checks (FP32's floor; early plateaus of the
+                               violation do not count); default 1e-5 */
   int32_t trace;            /* 1: record per-work-item timestamps of each
                                fused tiled sweep (cc_get_trace); default 0 */
   int32_t interleave;       /* tiled schedule: 1 = deal the objects over the
@@ -375,8 +377,10 @@ const char* cc_batch_last_error(const cc_batch* b);
  * outputs below `threshold` set to 0, pair duals 0, rebuild x and f from
  * them in FP64, run CC_WS_PAIR_PASSES pair passes (cc_pair_passes: the pair
  * duals settle to the predicted triangle duals) and reset the sweep count.  *candidates (nullable): the
- * number of candidate triplets.  Needs the tiled schedule, fused form and an
- * FP64 state (CC_ERR_UNSUPPORTED otherwise).  Synchronous.  Errors:
+ * number of candidate triplets.  Needs the tiled schedule, fused form and
+ * the dense store (CC_ERR_UNSUPPORTED otherwise).  In the FP32 bulk phase of
+ * CC_PREC_FP32_REFINE the same steps run on FP64 copies of the state and
+ * the result is rounded to FP32.  Synchronous.  Errors:
  * CC_ERR_ARG, CC_ERR_UNSUPPORTED, CC_ERR_OOM, CC_ERR_CUDA. */
 int cc_warm_start_mlp(cc_handle* h, const float* params, double threshold, int64_t* candidates);
 
@@ -385,7 +389,7 @@ int cc_warm_start_mlp(cc_handle* h, const float* params, double threshold, int64
  * triangle duals y of each candidate).  *count receives the number of
  * candidates; with feat and target NULL only the count is computed.
  * CC_ERR_ARG when cap < count (nothing written).  Synchronous; same
- * requirements as cc_warm_start_mlp. */
+ * requirements as cc_warm_start_mlp, and FP64 state. */
 int cc_ws_samples(cc_handle* h, float* feat, float* target, int64_t cap, int64_t* count);
 
 /* out[3q + r] = output r of the network (host params) on feature row q of

@@ -1159,9 +1159,11 @@ int cc_solve(cc_handle* h, double tol, int64_t max_sweeps, int64_t* sweeps_done)
       continue;
     }
     // FP32 bulk phase: refine in FP64 (from the converted duals) once the
-    // violation is small enough for FP32 or stops decreasing
-    const bool small = s.max_violation <= std::max(tol, h->o.refine_at);
-    const bool stalled = s.max_violation > 0.99 * prev_fp32;
+    // violation is small enough for FP32, or stops decreasing near that
+    // level (early plateaus of Dykstra's violation are not FP32's floor)
+    const double at = std::max(tol, h->o.refine_at);
+    const bool small = s.max_violation <= at;
+    const bool stalled = s.max_violation <= 100.0 * at && s.max_violation > 0.99 * prev_fp32;
     prev_fp32 = s.max_violation;
     if (small || stalled) {
       rc = switch_to_fp64(h);
@@ -1667,8 +1669,9 @@ int cc_batch_solve(cc_batch* b, double tol, int64_t max_sweeps, int64_t* sweeps_
       cc_stats s;
       check_finish(h, &s);
       if (h->fp32) {
-        const bool small = s.max_violation <= std::max(tol, b->o.refine_at);
-        const bool stalled = s.max_violation > 0.99 * b->prev_fp32[i];
+        const double at = std::max(tol, b->o.refine_at);
+        const bool small = s.max_violation <= at;
+        const bool stalled = s.max_violation <= 100.0 * at && s.max_violation > 0.99 * b->prev_fp32[i];
         b->prev_fp32[i] = s.max_violation;
         if (!(small || stalled)) continue;
         rc = switch_to_fp64(h);
@@ -1815,7 +1818,20 @@ void ws_release(cc_handle* h, WsCands& c) {
 }
 
 bool ws_usable(const cc_handle* h) {
-  return h->o.schedule == CC_SCHED_TILED && !h->o.exact && !h->fp32 && h->mask && h->o.problem == CC_PROB_CC;
+  return h->o.schedule == CC_SCHED_TILED && !h->o.exact && h->mask && h->o.problem == CC_PROB_CC;
+}
+
+template <int B>
+void rebuild_mask(cc_handle* h, bool f32) {
+  const int g = grid_for(h, h->mask_words, 256);
+  if (f32) k_rebuild_mask<float, B><<<g, 256, 0, h->st>>>((const float*)h->zt, h->mask, h->mask_words);
+  else k_rebuild_mask<double, B><<<g, 256, 0, h->st>>>((const double*)h->zt, h->mask, h->mask_words);
+}
+
+void rebuild_mask(cc_handle* h, bool f32) {
+  if (h->B == 8) rebuild_mask<8>(h, f32);
+  else if (h->B == 16) rebuild_mask<16>(h, f32);
+  else rebuild_mask<32>(h, f32);
 }
 
 }  // namespace
@@ -1825,7 +1841,7 @@ extern "C" {
 int cc_warm_start_mlp(cc_handle* h, const float* params, double threshold, int64_t* candidates) {
   if (!h) return fail(nullptr, CC_ERR_ARG, "handle is NULL");
   if (!params) return fail(h, CC_ERR_ARG, "params is NULL");
-  if (!ws_usable(h)) return fail(h, CC_ERR_UNSUPPORTED, "warm start needs the tiled schedule, fused form, FP64 state");
+  if (!ws_usable(h)) return fail(h, CC_ERR_UNSUPPORTED, "warm start needs the tiled schedule, fused form, dense store");
   CK(h, cudaSetDevice(h->dev));
   int rc = read_ctl_error(h);
   if (rc) return rc;
@@ -1837,6 +1853,29 @@ int cc_warm_start_mlp(cc_handle* h, const float* params, double threshold, int64
     ws_release(h, c);
     return fail(h, CC_ERR_OOM, "parameters");
   }
+  // FP32 bulk state: the same steps run on FP64 copies of the state, which
+  // are rounded to FP32 at the end (the bulk phase's precision)
+  const bool f32 = h->fp32;
+  void* keep[6] = {h->zt, h->zp, h->x, h->f, h->d, h->winv};
+  if (f32) {
+    const size_t te = (size_t)h->tile_elems;
+    void* t[4] = {dalloc(h, (size_t)h->zt_elems * sizeof(double)), dalloc(h, te * 2 * sizeof(double)),
+                  dalloc(h, te * sizeof(double)), dalloc(h, te * sizeof(double))};
+    if (!t[0] || !t[1] || !t[2] || !t[3]) {
+      for (void* q : t) dfree(h, q);
+      dfree(h, pd);
+      ws_release(h, c);
+      return fail(h, CC_ERR_OOM, "FP64 warm-start state");
+    }
+    h->zt = t[0];
+    h->zp = t[1];
+    h->x = t[2];
+    h->f = t[3];
+    h->d = h->d64;
+    h->winv = h->winv64;
+    h->fp32 = false;
+    h->esz = 8;
+  }
   CK(h, cudaMemcpyAsync(pd, params, WS_NPARAM * sizeof(float), cudaMemcpyHostToDevice, h->st));
   CK(h, cudaMemsetAsync(h->zt, 0, (size_t)h->zt_elems * sizeof(double), h->st));
   CK(h, cudaMemsetAsync(h->zp, 0, (size_t)h->tile_elems * 2 * sizeof(double), h->st));
@@ -1845,14 +1884,40 @@ int cc_warm_start_mlp(cc_handle* h, const float* params, double threshold, int64
     k_ws_infer<<<grid, 256, 0, h->st>>>(pd, c.feat, c.count, 1, nullptr, c.cand, (double*)h->zt, h->bt_rank, h->nb,
                                         h->B, h->o.eps, (float)threshold);
   }
-  CK(h, cudaGetLastError());
-  const int g2 = grid_for(h, h->mask_words, 256);
-  if (h->B == 8) k_rebuild_mask<double, 8><<<g2, 256, 0, h->st>>>((const double*)h->zt, h->mask, h->mask_words);
-  else if (h->B == 16) k_rebuild_mask<double, 16><<<g2, 256, 0, h->st>>>((const double*)h->zt, h->mask, h->mask_words);
-  else k_rebuild_mask<double, 32><<<g2, 256, 0, h->st>>>((const double*)h->zt, h->mask, h->mask_words);
-  CK(h, cudaGetLastError());
-  rc = resync_fp64(h);
+  rc = cudaGetLastError() == cudaSuccess ? CC_OK : fail(h, CC_ERR_CUDA, "warm-start inference");
+  if (rc == CC_OK) {
+    rebuild_mask(h, false);
+    rc = resync_fp64(h);
+  }
   if (rc == CC_OK) rc = cc_pair_passes(h, CC_WS_PAIR_PASSES);
+  if (f32) {   // round to FP32, back to the FP32 arrays; bits from the rounded duals
+    const size_t te = (size_t)h->tile_elems;
+    if (rc == CC_OK) {
+      k_convert<double, float><<<grid_for(h, h->zt_elems, 256), 256, 0, h->st>>>((const double*)h->zt, (float*)keep[0],
+                                                                              h->zt_elems);
+      k_convert<double, float><<<grid_for(h, 2 * te, 256), 256, 0, h->st>>>((const double*)h->zp, (float*)keep[1],
+                                                                          2 * (int64_t)te);
+      k_convert<double, float><<<grid_for(h, te, 256), 256, 0, h->st>>>((const double*)h->x, (float*)keep[2], te);
+      k_convert<double, float><<<grid_for(h, te, 256), 256, 0, h->st>>>((const double*)h->f, (float*)keep[3], te);
+    }
+    cudaStreamSynchronize(h->st);
+    dfree(h, h->zt);
+    dfree(h, h->zp);
+    dfree(h, h->x);
+    dfree(h, h->f);
+    h->zt = keep[0];
+    h->zp = keep[1];
+    h->x = keep[2];
+    h->f = keep[3];
+    h->d = keep[4];
+    h->winv = keep[5];
+    h->fp32 = true;
+    h->esz = 4;
+    if (rc == CC_OK) {
+      rebuild_mask(h, true);
+      rc = cudaGetLastError() == cudaSuccess ? CC_OK : fail(h, CC_ERR_CUDA, "FP32 warm-start state");
+    }
+  }
   CK(h, cudaStreamSynchronize(h->st));
   dfree(h, pd);
   ws_release(h, c);
@@ -1866,7 +1931,8 @@ int cc_warm_start_mlp(cc_handle* h, const float* params, double threshold, int64
 
 int cc_ws_samples(cc_handle* h, float* feat, float* target, int64_t cap, int64_t* count) {
   if (!h || !count) return fail(h, CC_ERR_ARG, "handle or count is NULL");
-  if (!ws_usable(h)) return fail(h, CC_ERR_UNSUPPORTED, "samples need the tiled schedule, fused form, FP64 state");
+  if (!ws_usable(h) || h->fp32)
+    return fail(h, CC_ERR_UNSUPPORTED, "samples need the tiled schedule, fused form, dense store, FP64 state");
   CK(h, cudaSetDevice(h->dev));
   int rc = read_ctl_error(h);
   if (rc) return rc;

@@ -213,6 +213,33 @@ def test_zero_prediction_is_the_cold_start_plus_pair_passes_bitwise():
         assert a.stats()["sweeps"] == 6
 
 
+def test_fp32_bulk_warm_start_is_the_fp64_one_rounded():
+    """In the FP32 bulk phase the warm start runs in FP64 and rounds its
+    result: x and f are the FP64 warm start's values rounded to FP32, the
+    duals within FP32 rounding; the solve then reaches the cold optimum."""
+    params = _trained()
+    n = 200
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=40)
+    with _solver(n, d, w, tile=16) as a, _solver(n, d, w, tile=16, precision="fp32_refine", check_every=5) as b:
+        b.sweep(3)                      # a bulk state to overwrite
+        ca = a.warm_start(params, threshold=1e-3)
+        cb = b.warm_start(params, threshold=1e-3)
+        assert ca == cb > 0
+        xa, fa = a.get_x()
+        xb, fb = b.get_x()
+        np.testing.assert_array_equal(xb, xa.astype(np.float32).astype(np.float64))
+        np.testing.assert_array_equal(fb, fa.astype(np.float32).astype(np.float64))
+        for u, v in zip(b.get_duals(), a.get_duals()):
+            np.testing.assert_allclose(u, v, rtol=2e-7, atol=0)
+        assert b.stats()["sweeps"] == 0
+        ok, k = b.solve(1e-4, 20000)
+        assert ok and b.stats()["fp32_sweeps"] > 0
+        with _solver(n, d, w, tile=16, check_every=5) as c:
+            assert c.solve(1e-7, 20000)[0]
+            lp = c.check()["lp_objective"]
+        assert abs(b.check()["lp_objective"] - lp) <= 1e-4 * abs(lp)
+
+
 def test_warm_start_rejects_the_exact_form():
     import paper_1901_10084_gb300 as cc
     from paper_1901_10084_gb300 import warmstart
