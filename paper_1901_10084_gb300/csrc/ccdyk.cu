@@ -1876,15 +1876,17 @@ int cc_warm_start_mlp(cc_handle* h, const float* params, double threshold, int64
     h->fp32 = false;
     h->esz = 8;
   }
-  CK(h, cudaMemcpyAsync(pd, params, WS_NPARAM * sizeof(float), cudaMemcpyHostToDevice, h->st));
-  CK(h, cudaMemsetAsync(h->zt, 0, (size_t)h->zt_elems * sizeof(double), h->st));
-  CK(h, cudaMemsetAsync(h->zp, 0, (size_t)h->tile_elems * 2 * sizeof(double), h->st));
-  if (c.count > 0) {
+  // errors from here on fall through to the restore below
+  cudaError_t ce = cudaMemcpyAsync(pd, params, WS_NPARAM * sizeof(float), cudaMemcpyHostToDevice, h->st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(h->zt, 0, (size_t)h->zt_elems * sizeof(double), h->st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(h->zp, 0, (size_t)h->tile_elems * 2 * sizeof(double), h->st);
+  if (ce == cudaSuccess && c.count > 0) {
     const int grid = (int)std::min<int64_t>((c.count + 127) / 128, (int64_t)h->sms * 8);
     k_ws_infer<<<grid, 256, 0, h->st>>>(pd, c.feat, c.count, 1, nullptr, c.cand, (double*)h->zt, h->bt_rank, h->nb,
                                         h->B, h->o.eps, (float)threshold);
   }
-  rc = cudaGetLastError() == cudaSuccess ? CC_OK : fail(h, CC_ERR_CUDA, "warm-start inference");
+  if (ce == cudaSuccess) ce = cudaGetLastError();
+  rc = ce == cudaSuccess ? CC_OK : fail(h, CC_ERR_CUDA, "warm-start inference");
   if (rc == CC_OK) {
     rebuild_mask(h, false);
     rc = resync_fp64(h);
@@ -1913,10 +1915,9 @@ int cc_warm_start_mlp(cc_handle* h, const float* params, double threshold, int64
     h->winv = keep[5];
     h->fp32 = true;
     h->esz = 4;
-    if (rc == CC_OK) {
-      rebuild_mask(h, true);
-      rc = cudaGetLastError() == cudaSuccess ? CC_OK : fail(h, CC_ERR_CUDA, "FP32 warm-start state");
-    }
+    rebuild_mask(h, true);   // also after a failure: the bits then describe the FP32 duals kept
+    const int r2 = cudaGetLastError() == cudaSuccess ? CC_OK : fail(h, CC_ERR_CUDA, "FP32 warm-start state");
+    if (rc == CC_OK) rc = r2;
   }
   CK(h, cudaStreamSynchronize(h->st));
   dfree(h, pd);
