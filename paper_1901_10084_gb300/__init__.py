@@ -17,7 +17,8 @@ from ._native import (CCError, CC_OK, CC_ERR_ARG, CC_ERR_OOM, CC_ERR_CUDA, CC_ER
                       CC_SCHED_SUMMOD, CC_SCHED_TILED, CC_PREC_FP64, CC_PREC_FP32_REFINE,
                       cc_opts_default, cc_create, cc_create_device, cc_sweep, cc_check, cc_solve,
                       cc_get_x, cc_get_duals, cc_set_state, cc_get_stats, cc_device_bytes,
-                      cc_destroy, cc_last_error, cc_refine_fp64, cc_set_duals, cc_check_noalloc)
+                      cc_destroy, cc_last_error, cc_refine_fp64, cc_set_duals, cc_check_noalloc,
+                      cc_pair_passes)
 from .buildlib import build
 
 __all__ = [
@@ -25,6 +26,7 @@ __all__ = [
     "cc_opts_default", "cc_create", "cc_create_device", "cc_sweep", "cc_check", "cc_solve",
     "cc_get_x", "cc_get_duals", "cc_set_state", "cc_get_stats", "cc_device_bytes",
     "cc_destroy", "cc_last_error", "cc_refine_fp64", "cc_set_duals", "cc_check_noalloc",
+    "cc_pair_passes",
 ]
 
 SCHEDULES = {"diagonal": CC_SCHED_DIAGONAL, "summod": CC_SCHED_SUMMOD, "tiled": CC_SCHED_TILED}
@@ -131,7 +133,7 @@ class Solver:
 
     def pair_passes(self, passes: int) -> None:
         """Visit the pair rows alone `passes` times (see cc_pair_passes)."""
-        _native.cc_pair_passes(self.h, passes)
+        cc_pair_passes(self.h, passes)
 
     def check(self) -> dict:
         return cc_check(self.h).as_dict()
