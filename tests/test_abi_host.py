@@ -112,3 +112,28 @@ def test_checked_library_exports_the_same_symbols(lib):
         assert hasattr(chk, name), name
     src = open(os.path.join(ROOT, "include", "ccdyk.h")).read()
     assert re.search(r"#define CC_ERR_BOUNDS 7\b", src)
+
+
+def _declarations():
+    """name -> number of parameters, for every function include/ccdyk.h declares."""
+    src = open(os.path.join(ROOT, "include", "ccdyk.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(?:int|int32_t|int64_t|void|const char|cc_opts|cc_handle)\s*\**\s*(cc_[a-z0-9_]+)\s*"
+                         r"\(([^;{]*?)\)\s*;", src, flags=re.S):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_bindings_pass_as_many_arguments_as_the_header_declares(lib):
+    decl = _declarations()
+    assert set(decl) == set(_declared())
+    checked = 0
+    for name, count in decl.items():
+        fn = getattr(lib, name)
+        if fn.argtypes is None:
+            continue
+        assert len(fn.argtypes) == count, (name, len(fn.argtypes), count)
+        checked += 1
+    assert checked >= 20
