@@ -137,3 +137,30 @@ def test_bindings_pass_as_many_arguments_as_the_header_declares(lib):
         assert len(fn.argtypes) == count, (name, len(fn.argtypes), count)
         checked += 1
     assert checked >= 20
+
+
+@pytest.mark.parametrize("struct", ["cc_opts", "cc_stats"])
+def test_struct_layout_matches_the_header(struct):
+    """The ctypes mirrors of the option and statistics structs against the C
+    compiler's layout of include/ccdyk.h: size and every field's offset."""
+    import shutil
+    import subprocess
+    from paper_1901_10084_gb300 import _native as N
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    cls = getattr(N, struct)
+    names = [f for f, _ in cls._fields_]
+    work = os.path.join(ROOT, "tests", "_build")
+    os.makedirs(work, exist_ok=True)
+    prog = __import__("pathlib").Path(work) / f"layout_{struct}_{os.getpid()}.c"
+    prog.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"ccdyk.h\"\nint main(void) {\n"
+                    f"  printf(\"%zu\\n\", sizeof({struct}));\n"
+                    + "".join(f"  printf(\"%zu\\n\", offsetof({struct}, {f}));\n" for f in names)
+                    + "  return 0;\n}\n")
+    exe = prog.with_suffix("")
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(prog)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    prog.unlink()
+    exe.unlink()
+    assert got[0] == ctypes.sizeof(cls)
+    assert got[1:] == [getattr(cls, f).offset for f in names]

@@ -67,11 +67,14 @@ def test_reference_arm_runs_on_rank_zero_only():
     assert out["impl"] == "reference" and out["value"] > 0
 
 
-def test_host_cores_reads_the_cgroup_quota(tmp_path):
+def test_host_cores_reads_the_cgroup_quota():
     sys.path.insert(0, ROOT)
+    import pathlib
     import bench
-    f = tmp_path / "cpu.max"
-    free = bench.host_cores(str(tmp_path / "absent"))
+    work = pathlib.Path(ROOT) / "tests" / "_build"
+    work.mkdir(exist_ok=True)
+    f = work / f"cpu.max.{os.getpid()}"
+    free = bench.host_cores(str(work / "absent"))
     assert free >= 1
     f.write_text("max 100000\n")
     assert bench.host_cores(str(f)) == free
@@ -79,3 +82,4 @@ def test_host_cores_reads_the_cgroup_quota(tmp_path):
     assert bench.host_cores(str(f)) == min(free, 2)
     f.write_text("50000 100000\n")
     assert bench.host_cores(str(f)) == 1
+    f.unlink()
