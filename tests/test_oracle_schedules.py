@@ -6,6 +6,7 @@ import json
 import os
 from collections import defaultdict
 
+import numpy as np
 import pytest
 
 import oracle
@@ -128,3 +129,50 @@ def test_schedule2_subphases_in_order(n, B):
         sub = (i % B + j % B + k % B) % B
         assert sub >= last.get(bt, -1)
         last[bt] = sub
+
+
+def _ranks(n, rec):
+    """Lexicographic rank of each (i, j, k) row of an order record (vectorized)."""
+    i, j, k = (rec[:, c].astype(np.int64) for c in (1, 2, 3))
+    c3 = lambda m: m * (m - 1) * (m - 2) // 6
+    c2 = lambda m: m * (m - 1) // 2
+    return (c3(n) - c3(n - i)) + (c2(n - 1 - i) - c2(n - j)) + (k - j - 1)
+
+
+@pytest.mark.parametrize("n", [99, 150, 200])
+@pytest.mark.parametrize("schedule,tile", [(0, 0), (1, 0), (2, 16)])
+def test_large_n_every_triplet_once_and_phases_conflict_free(n, schedule, tile):
+    """Sizes up to n = 200 (n = 99 and 150 are multiples of 3): every i<j<k
+    exactly once (the canonical ranks are a permutation, checked against
+    oracle.trank on a sample), and inside a phase no pair is touched twice,
+    except within one set S_{i,k} of schedule 0, whose triplets share x_ik
+    and run in order."""
+    rec = oracle.order(n, schedule, tile).astype(np.int64)
+    T = n * (n - 1) * (n - 2) // 6
+    assert rec.shape[0] == T
+    assert np.all((rec[:, 1] < rec[:, 2]) & (rec[:, 2] < rec[:, 3]))
+    r = _ranks(n, rec)
+    assert np.array_equal(np.sort(r), np.arange(T))
+    for t in np.random.default_rng(n).integers(0, T, 20):
+        assert oracle.trank(n, *(int(v) for v in rec[t, 1:])) == r[t]
+    ph, i, j, k = rec[:, 0], rec[:, 1], rec[:, 2], rec[:, 3]
+    pid = lambda a, b: a * n + b
+    if schedule == 0:   # pairs (i, j) and (j, k) once per phase; (i, k) once per set
+        keys = np.concatenate([ph * n * n + pid(i, j), ph * n * n + pid(j, k)])
+        assert np.unique(keys).size == keys.size
+        setkey = ph * n * n + pid(i, k)
+        starts = np.r_[True, setkey[1:] != setkey[:-1]]
+        assert np.unique(setkey[starts]).size == starts.sum()     # each set contiguous, once
+    elif schedule == 1:
+        keys = np.concatenate([ph * n * n + pid(i, j), ph * n * n + pid(i, k), ph * n * n + pid(j, k)])
+        assert np.unique(keys).size == keys.size
+        assert np.all((i + j + k) % n == ph)
+    else:               # tiled: phase x sub-phase units touch each pair once
+        B = tile
+        sub = (i % B + j % B + k % B) % B
+        blk = (i // B) * n * n + (j // B) * n + (k // B)
+        unit = (ph * n * n * n + blk) * B + sub
+        keys = np.concatenate([unit * n * n + pid(i, j), unit * n * n + pid(i, k), unit * n * n + pid(j, k)])
+        assert np.unique(keys).size == keys.size
+        tkeys = np.unique(np.stack([ph, blk]), axis=1)
+        assert tkeys.shape[1] == np.unique(blk).size              # each block triple in one phase
