@@ -22,7 +22,8 @@ Parity status of each function:
   * ``order`` / ``num_phases``: pinned (brute-force coverage and
     conflict-freeness, the phase counts and set sizes the paper states).
   * ``max_violation`` / ``objectives``: pinned by direct definition checks
-    against the dense constraint matrix.
+    against the dense constraint matrix; the threaded ``max_violation`` is
+    pinned to the serial one (equal values) in ``tests/test_oracle_threads.py``.
 """
 from __future__ import annotations
 
@@ -94,6 +95,8 @@ def _load():
         lib.ora_sweep_threads.restype = i64
         lib.ora_sweep_l2_threads.argtypes = [i64, i32, i64, dp, dp, dp, i32, i64]
         lib.ora_sweep_l2_threads.restype = i64
+        lib.ora_max_violation_threads.argtypes = [i64, dp, i32]
+        lib.ora_max_violation_threads.restype = dbl
         _lib = lib
         return lib
 
@@ -215,6 +218,32 @@ class State:
             if s % check_every == 0 and self.max_violation() <= tol:
                 return s
         return -1
+
+
+def max_violation(n: int, x: np.ndarray, threads: int = 1) -> float:
+    """Largest metric-row violation max(0, x_h - x_a - x_b) over every
+    triplet and hypotenuse of the packed distances x (no State, so no dual
+    storage); with ``threads`` > 1 the first indices are dealt to host
+    threads (a maximum is order-free: the same value)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    assert x.shape == (num_pairs(n),)
+    if threads <= 1:
+        return float(_load().ora_max_violation(n, _dp(x)))
+    m = float(_load().ora_max_violation_threads(n, _dp(x), threads))
+    if m < 0:
+        raise RuntimeError("could not start the oracle's threads")
+    return m
+
+
+def objectives(n: int, eps: float, d, w, x, f, ypair) -> dict:
+    """The CC objectives of State.objectives on given arrays (packed pairs;
+    ypair 2 per pair)."""
+    c = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    d, w, x, f, ypair = c(d), c(w), c(x), c(f), c(ypair)
+    out = np.zeros(5)
+    _load().ora_objectives(n, float(eps), _dp(d), _dp(w), _dp(x), _dp(f), _dp(ypair), _dp(out))
+    return {"lp": out[0], "qp_primal": out[1], "dual": out[2],
+            "pair_violation": out[3], "wf": out[4], "gap": out[1] - out[2]}
 
 
 def order(n: int, schedule: int, tile: int = 16) -> np.ndarray:

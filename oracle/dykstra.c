@@ -24,10 +24,13 @@
  * Visiting order ("schedules", Sec. III-B): a sweep visits every triplet once
  * and, for each triplet, its three rows in the order hypotenuse = ij, ik, jk;
  * after all triplets it visits every pair's two rows (x - f <= d first).
- *   0: the paper's diagonal listing of the sets S_{i,k} (Fig. "for"): first
- *      loop x = 1, z = n..3; second loop z = n, x = 2..n-2; inner loop over
- *      c = 0..floor((z-x-2)/2) with i = x+c, k = z-c; the triplets of one set
- *      S_{i,k} in ascending middle index j.
+ *   0: the paper's diagonal schedule (Sec. III-B): the set S_{i,k} holds
+ *      the triplets (i, j, k), i < j < k, of one outer pair (i, k); two sets
+ *      on one anti-diagonal i + k = s of the (i, k) grid share no pair, so a
+ *      diagonal is a phase.  With 1-based indices the phases are s = n+1 down
+ *      to 4, then s = n+2 up to 2n-2 (2n-5 phases, every (i, k) with
+ *      k >= i+2 on exactly one of them); inside a phase the sets come by
+ *      ascending i, inside a set the triplets by ascending middle index j.
  *   1: triplets grouped by (i+j+k) mod n; phase s = 0..n-1, inside a phase in
  *      ascending (i, j).  Two triplets of one phase that share two indices
  *      share the third, so a phase touches every pair at most once (the
@@ -209,33 +212,27 @@ static int walk_step(walk_t* w, int64_t i, int64_t j, int64_t k) {
   return 1;
 }
 
-/* Schedule 0: the listing of Fig. "for" with 1-based x, z, c, i, k as printed. */
+/* Schedule 0, one phase: the sets S_{i,k} on the anti-diagonal i + k = s
+ * (1-based), i.e. every i with 1 <= i, k = s - i <= n and k - i >= 2, by
+ * ascending i; each set is a serial chain over j = i+1 .. k-1. */
+static int walk_diagonal(walk_t* w, int64_t s) {
+  const int64_t n = w->n;
+  for (int64_t i = (s - n > 1 ? s - n : 1); s - i - i >= 2; ++i) {
+    const int64_t k = s - i;
+    unit_begin(w);
+    for (int64_t j = i + 1; j < k; ++j)
+      if (!walk_step(w, i - 1, j - 1, k - 1)) return 0;   /* stored 0-based */
+  }
+  return end_phase(w);
+}
+
+/* Schedule 0: the diagonals s = n+1, n, ..., 4, then s = n+2, ..., 2n-2. */
 static int walk_sched0(walk_t* w) {
-  int64_t n = w->n;
-  int64_t x = 1, z, c, g, i, k, j;
-  for (z = n; z >= 3; --z) {                 /* first double loop */
-    g = (z - x - 2) / 2;
-    for (c = 0; c <= g; ++c) {
-      i = x + c;
-      k = z - c;
-      unit_begin(w);
-      for (j = i + 1; j <= k - 1; ++j)       /* the set S_{i,k} */
-        if (!walk_step(w, i - 1, j - 1, k - 1)) return 0;
-    }
-    if (!end_phase(w)) return 0;
-  }
-  z = n;
-  for (x = 2; x <= n - 2; ++x) {             /* second double loop */
-    g = (z - x - 2) / 2;
-    for (c = 0; c <= g; ++c) {
-      i = x + c;
-      k = z - c;
-      unit_begin(w);
-      for (j = i + 1; j <= k - 1; ++j)
-        if (!walk_step(w, i - 1, j - 1, k - 1)) return 0;
-    }
-    if (!end_phase(w)) return 0;
-  }
+  const int64_t n = w->n;
+  for (int64_t s = n + 1; s >= 4; --s)
+    if (!walk_diagonal(w, s)) return 0;
+  for (int64_t s = n + 2; s <= 2 * n - 2; ++s)
+    if (!walk_diagonal(w, s)) return 0;
   return 1;
 }
 
@@ -519,4 +516,65 @@ int64_t ora_sweep_threads(int64_t n, int sched, int64_t B, double eps, const dou
 int64_t ora_sweep_l2_threads(int64_t n, int sched, int64_t B, const double* winv, double* x,
                              double* ytri, int nthr, int64_t max_phases) {
   return sweep_threads(n, sched, B, 1.0, NULL, winv, x, NULL, ytri, NULL, nthr, max_phases);
+}
+
+/* ---- threaded largest violation -------------------------------------------
+ * ora_max_violation with the first indices i dealt round-robin to nthr
+ * threads, each keeping its own maximum; a maximum does not depend on the
+ * order it is taken in, so the result equals the serial one exactly. */
+typedef struct {
+  int64_t n;
+  const double* x;
+  int nthr, tid;
+  double m;
+} maxv_job;
+
+static void* maxv_main(void* arg) {
+  maxv_job* t = (maxv_job*)arg;
+  const int64_t n = t->n;
+  const double* x = t->x;
+  double m = 0.0;
+  for (int64_t i = t->tid; i < n; i += t->nthr)
+    for (int64_t j = i + 1; j < n; ++j)
+      for (int64_t k = j + 1; k < n; ++k) {
+        double xij = x[pidx(n, i, j)], xik = x[pidx(n, i, k)], xjk = x[pidx(n, j, k)];
+        double v0 = xij - xik - xjk, v1 = xik - xij - xjk, v2 = xjk - xij - xik;
+        if (v0 > m) m = v0;
+        if (v1 > m) m = v1;
+        if (v2 > m) m = v2;
+      }
+  t->m = m;
+  return NULL;
+}
+
+/* Returns -1 when the threads could not be started. */
+double ora_max_violation_threads(int64_t n, const double* x, int nthr) {
+  if (nthr < 1) nthr = 1;
+  maxv_job* jobs = (maxv_job*)calloc((size_t)nthr, sizeof(maxv_job));
+  pthread_t* ids = (pthread_t*)calloc((size_t)nthr, sizeof(pthread_t));
+  if (!jobs || !ids) {
+    free(jobs);
+    free(ids);
+    return -1.0;
+  }
+  for (int t = 0; t < nthr; ++t) {
+    jobs[t].n = n;
+    jobs[t].x = x;
+    jobs[t].nthr = nthr;
+    jobs[t].tid = t;
+  }
+  int made = 1, ok = 1;
+  for (; made < nthr; ++made)
+    if (pthread_create(&ids[made], NULL, maxv_main, &jobs[made]) != 0) {
+      ok = 0;
+      break;
+    }
+  maxv_main(&jobs[0]);
+  for (int t = 1; t < made; ++t) pthread_join(ids[t], NULL);
+  double m = 0.0;
+  for (int t = 0; t < nthr && ok; ++t)
+    if (jobs[t].m > m) m = jobs[t].m;
+  free(jobs);
+  free(ids);
+  return ok ? m : -1.0;
 }

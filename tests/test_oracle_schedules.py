@@ -29,14 +29,14 @@ def test_each_triplet_exactly_once(n, schedule, tile):
 
 @pytest.mark.parametrize("n", range(3, 40))
 def test_phase_counts(n):
-    assert oracle.num_phases(n, 0) == 2 * n - 5       # z = n..3, then x = 2..n-2
+    assert oracle.num_phases(n, 0) == 2 * n - 5       # diagonals n+1..4, then n+2..2n-2
     assert oracle.num_phases(n, 1) == n
     for B in (2, 4, 7):
         assert oracle.num_phases(n, 2, B) == -(-n // B)
 
 
 @pytest.mark.parametrize("n", [3, 4, 9, 12, 13, 20, 33])
-def test_schedule0_follows_the_diagonal_listing(n):
+def test_schedule0_phases_are_the_diagonals(n):
     """Phases of schedule 0 are the diagonals i+k = const (1-based): first
     n+1 down to 4, then n+2 up to 2n-2; inside a phase the sets S_{i,k} come
     in ascending i, and a set's triplets in ascending j."""

@@ -77,3 +77,17 @@ def test_threaded_solve_reaches_the_serial_result():
         b.sweep_threads(1, threads=5)
     _same(a, b)
     assert a.objectives() == b.objectives()
+
+
+@pytest.mark.parametrize("n", [3, 4, 23, 64])
+@pytest.mark.parametrize("threads", [1, 2, 5, 16])
+def test_threaded_max_violation_equals_serial(n, threads):
+    """The threaded largest violation (first indices dealt to threads) is the
+    serial one, exactly: a maximum does not depend on the order."""
+    rng = np.random.default_rng(n * 31 + threads)
+    x = rng.uniform(0.0, 1.0, oracle.num_pairs(n))
+    serial = oracle.max_violation(n, x)
+    assert oracle.max_violation(n, x, threads=threads) == serial
+    st = oracle.State(n, np.ones(oracle.num_pairs(n)), np.ones(oracle.num_pairs(n)), 0.2)
+    st.x[:] = x
+    assert st.max_violation() == serial
