@@ -56,6 +56,8 @@ def parse():
                    help="skip the FP32 bulk + FP64 refinement time-to-tolerance solve")
     p.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
     p.add_argument("--no-chain", action="store_true", help="skip the dependency-chain analysis of a traced sweep")
+    p.add_argument("--no-c3", action="store_true",
+                   help="skip the Chung-Lu n=3000 weighted precision-form solve (dense FP32 / FP64 stores)")
     p.add_argument("--batch-count", type=int, default=256)
     p.add_argument("--no-warm-start", action="store_true", help="skip the learned warm-start measurement")
     p.add_argument("--no-l2", action="store_true", help="skip the l2 metric nearness measurement")
@@ -218,6 +220,7 @@ def run_ours(args, rank, world, local_rank):
         dual_bytes = DUAL_BYTES_FP64 if args.precision == "fp64" else DUAL_BYTES_FP64 // 2
         achieved_hbm = dual_bytes * T / (avg_sweep * 1e-3) / 1e9
         traffic = _profiled_traffic(args)
+        measured_gbs = traffic / (avg_sweep * 1e-3) / 1e9 if traffic else None
         kernel = SWEEP_KERNEL[args.schedule]
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -232,13 +235,27 @@ def run_ours(args, rank, world, local_rank):
                              "within a sweep x (%.1f MB) stays L2-resident by design" % (8 * n * n / 2 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single"},
             "sweep_ms": {"mean": avg_sweep, "min": min(sweep_ms), "max": max(sweep_ms)},
-            "roofline": {"bound": "hbm", "achieved": achieved_hbm, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved_hbm / hbm_peak, "traffic": traffic, "kernel": kernel,
-                         "algorithmic": f"{dual_bytes} B per triplet (3 duals read + 3 written) x {T} "
-                                        "triplets per launch; the kernel moves only the nonzero-dual "
-                                        "bitmask and the nonzero duals, so traffic is far below it",
+            "value_note": "equal-result rate: every one of the C(n,3) triplets of a sweep counts as one "
+                          "projection; the filters skip the triplets whose update is proved a no-op (about "
+                          "1 % are updated), with values equal to the unfiltered sweep's",
+            "roofline": {"bound": "hbm", "achieved": measured_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": measured_gbs / hbm_peak if measured_gbs is not None else None,
+                         "traffic": traffic, "kernel": kernel,
+                         "achieved_from": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one sweep launch "
+                                          "(profiles/traffic.json, same kernel and workload) / mean timed sweep",
                          "peak_source": ("of measured: MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in pk
-                                         else "of fallback")},
+                                         else "of fallback"),
+                         "binding": "dependency chain: every tile is visited once per phase, so a sweep is "
+                                    "the Nb-long chain of dependent block triples per tile; chain_frac = "
+                                    "that chain's own work / sweep span (traced sweep, see chain)",
+                         "chain_frac": None,
+                         "dense_equivalent": {
+                             "achieved": achieved_hbm, "frac": achieved_hbm / hbm_peak, "unit": "GB/s",
+                             "algorithmic": f"{dual_bytes} B per triplet (3 duals read + 3 written) x {T} "
+                                            "triplets per launch, the bytes an unfiltered dense sweep would "
+                                            "move; the kernel proves most rows inactive from the nonzero-dual "
+                                            "bitmask and float copies of x and moves only the bitmask and the "
+                                            "nonzero duals"}},
             "roofline_alu": {"bound": "alu", "achieved": achieved_alu, "peak": fp64_peak,
                              "unit": "Tinst/s (FP64 pipe)", "frac": achieved_alu / fp64_peak,
                              "peak_source": "derived: 152 SMs x 2 FP64 instructions/clk x 2070 MHz "
@@ -278,6 +295,9 @@ def run_ours(args, rank, world, local_rank):
             out["precision_form"] = pf
     if rank == 0 and not args.no_chain and args.schedule == "tiled":
         out["chain"] = _chain(args, n, d, w, stream)
+        out["roofline"]["chain_frac"] = out["chain"]["after_60_sweeps"]["chain_frac"]
+    if rank == 0 and not args.no_c3 and args.schedule == "tiled" and args.precision == "fp64":
+        out["precision_form_c3"] = _c3(args, stream)
     if rank == 0 and not args.no_batch and args.schedule == "tiled":
         out["batched_form"] = _batched(args, stream)
     if rank == 0 and not args.no_warm_start and args.schedule == "tiled":
@@ -286,10 +306,105 @@ def run_ours(args, rank, world, local_rank):
         out["l2_nearness"] = _l2(args, stream)
     if rank == 0 and not args.no_sparse and args.schedule == "tiled":
         out["sparse_store"] = _sparse(args, stream)
+    if rank == 0:
+        out = _lead_with_time_to_tol(out)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
     return out
+
+
+def _lead_with_time_to_tol(out):
+    """Put the time-to-tolerance figures of every form (with each form's LP
+    objective error against the plain FP64 solve) right after the metric's
+    value: they are the measure the method is judged by."""
+    summ = {}
+    ttt = out.get("time_to_tol")
+    if ttt:
+        summ["chunglu1000_fp64"] = {"seconds": ttt["seconds"], "sweeps": ttt["sweeps"],
+                                    "max_violation": ttt["max_violation"]}
+    pf = out.get("precision_form")
+    if pf:
+        summ["chunglu1000_fp32_refine"] = {"seconds": pf["seconds"], "sweeps": pf["sweeps"],
+                                           "fp32_sweeps": pf.get("fp32_sweeps"),
+                                           "lp_objective_rel_vs_fp64": pf["error_vs_fp64"]["lp_objective_rel"],
+                                           "speedup_vs_fp64": pf["speedup_vs_fp64"]}
+    ws = out.get("warm_start") or {}
+    for name in ("chunglu1000", "chunglu2000"):
+        r = ws.get(name)
+        if not r:
+            continue
+        for mode in ("cold", "warm", "warm_fp32", "cold_fp32"):
+            if mode in r:
+                e = {"seconds": r[mode]["seconds"], "sweeps": r[mode]["sweeps"]}
+                if mode != "cold":
+                    e["lp_objective_rel_vs_fp64"] = (abs(r[mode]["lp_objective"] - r["cold"]["lp_objective"])
+                                                     / abs(r["cold"]["lp_objective"]))
+                summ[f"{name}_{'fp64' if mode == 'cold' else mode}"] = e
+    c3 = out.get("precision_form_c3")
+    if c3:
+        for prec in ("fp64", "fp32_refine"):
+            e = {"seconds": c3[prec]["seconds"], "sweeps": c3[prec]["sweeps"]}
+            if prec == "fp32_refine":
+                e["lp_objective_rel_vs_fp64"] = c3["error_vs_fp64"]["lp_objective_rel"]
+            summ[f"chunglu3000w_{prec}"] = e
+    if not summ:
+        return out
+    summ["note"] = ("wall time of cc_solve (warm: including the warm start) to max metric violation <= tol; "
+                    "each form's LP objective against the plain FP64 GPU solve of the same instance")
+    lead = {}
+    for k, v in out.items():
+        lead[k] = v
+        if k == "unit":
+            lead["time_to_tol_summary"] = summ
+    return lead
+
+
+def _c3(args, stream):
+    """The precision form's own configuration: Chung-Lu n = 3000 (exponent
+    2.5, mean degree 10, seed 2, w ~ U[0.5, 2]) with the dense dual store,
+    solved to the tolerance in plain FP64 and in the FP32 bulk form (FP32 x
+    and dense FP32 duals, about 54 GB) with FP64 refinement; the error of
+    the refined result against the FP64 GPU solve (objective, x, violation).
+    The oracle needs about half a minute per sweep on 16 host cores at this
+    size; its one-sweep agreement with the GPU at n = 3000 is a GPU test
+    (tests/test_gpu_parity.py), and the FP64 GPU solve is pinned to the
+    oracle at convergence on the n = 1000 workload."""
+    import numpy as np
+    import torch
+
+    import paper_1901_10084_gb300 as cc
+    from instances import workload
+    n, d, w, desc = workload("chunglu3000w")
+    T = n * (n - 1) * (n - 2) // 6
+    rec = {"desc": desc, "triplets": T, "tol": args.tol, "check_every": args.check_every, "tile": args.tile,
+           "store": "dense"}
+    xs = {}
+    for prec in ("fp64", "fp32_refine"):
+        torch.cuda.empty_cache()
+        with cc.Solver(n, d, w, eps=0.2, tile=args.tile, precision=prec, check_every=args.check_every,
+                       stream=stream) as s:
+            bytes0 = s.device_bytes()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            conv, k = s.solve(args.tol, args.ttt_max_sweeps)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t
+            st = s.check()
+            xs[prec] = s.get_x()[0]
+            rec[prec] = {"seconds": el, "sweeps": k, "converged": conv, "fp32_sweeps": st["fp32_sweeps"],
+                         "max_violation": st["max_violation"], "lp_objective": st["lp_objective"],
+                         "gap": st["gap"], "device_bytes_at_create": bytes0,
+                         "device_bytes_at_end": s.device_bytes(), "last_sweep_ms": st["last_sweep_ms"]}
+        torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    a, b = rec["fp64"], rec["fp32_refine"]
+    rec["error_vs_fp64"] = {"lp_objective_rel": abs(b["lp_objective"] - a["lp_objective"]) / abs(a["lp_objective"]),
+                            "x_max_abs": float(np.max(np.abs(xs["fp32_refine"] - xs["fp64"]))),
+                            "max_violation": b["max_violation"],
+                            "reference": "the plain FP64 GPU solve of the same instance (dense store)"}
+    rec["speedup_vs_fp64"] = a["seconds"] / b["seconds"]
+    return rec
 
 
 def _chain(args, n, d, w, stream):
@@ -395,6 +510,17 @@ def _warm_start(args, stream):
     rec["train_steps"] = args.ws_steps
     _, rec["loss"] = warmstart.grad(params, feat, targ)
     rec["loss_zero_prediction"] = float((targ.double() ** 2).mean())
+    # ablation baselines with the same pair passes and threshold: a trivial
+    # predictor of the d pattern (dual c on the row whose hypotenuse is the
+    # one non-edge of a triplet whose other two pairs are edges, the rows a
+    # cold start violates first; c = the mean training dual of those rows)
+    # and the all-zero prediction
+    c_pat, n_pat = warmstart.dpattern_constant(feat, targ)
+    p_pat = warmstart.dpattern_params(c_pat)
+    _, rec["loss_dpattern_predictor"] = warmstart.grad(p_pat, feat, targ)
+    rec["dpattern_constant"] = c_pat
+    rec["dpattern_rows"] = n_pat
+    p_zero = warmstart.init_params(0)
     del feat, targ
     torch.cuda.empty_cache()
     for name, n, seed in (("chunglu1000", 1000, 1), ("chunglu2000", 2000, 4)):
@@ -415,6 +541,24 @@ def _warm_start(args, stream):
         r["speedup"] = r["cold"]["seconds"] / r["warm"]["seconds"]
         r["lp_objective_rel_vs_cold"] = (abs(r["warm"]["lp_objective"] - r["cold"]["lp_objective"])
                                          / abs(r["cold"]["lp_objective"]))
+        # ablation: the same warm-start path (features, inference kernel,
+        # threshold, rebuild, 16 pair passes) with the trivial predictor and
+        # with an all-zero prediction (threshold above every output)
+        abl = {}
+        for mode, pp, thr in (("dpattern", p_pat, args.ws_threshold), ("zero", p_zero, 1e30)):
+            with cc.Solver(n, d, w, tile=args.tile, check_every=5, stream=stream) as s:
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                s.warm_start(pp, thr)
+                ok, k = s.solve(args.tol, args.ttt_max_sweeps)
+                torch.cuda.synchronize()
+                lp = s.check()["lp_objective"]
+                abl[mode] = {"seconds": time.perf_counter() - t, "sweeps": k, "converged": ok,
+                             "lp_objective_rel_vs_cold": abs(lp - r["cold"]["lp_objective"])
+                             / abs(r["cold"]["lp_objective"])}
+        abl["network"] = {"seconds": r["warm"]["seconds"], "sweeps": r["warm"]["sweeps"],
+                          "lp_objective_rel_vs_cold": r["lp_objective_rel_vs_cold"]}
+        r["ablation"] = abl
         # the FP32 bulk form, cold and warm-started (the warm start runs in FP64 and is rounded)
         for mode in ("cold_fp32", "warm_fp32"):
             with cc.Solver(n, d, w, tile=args.tile, check_every=5, stream=stream, precision="fp32_refine") as s:

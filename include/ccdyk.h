@@ -67,7 +67,7 @@ extern "C" {
 /* Visiting orders (Sec. III-B/C).  Every schedule visits each triplet once
  * per sweep; triplets of one phase touch pairwise-disjoint pairs, so a phase
  * runs in parallel with the same result as any serial order of it. */
-#define CC_SCHED_DIAGONAL 0 /* the paper's listing: phases are the diagonals
+#define CC_SCHED_DIAGONAL 0 /* the paper's schedule: phases are the diagonals
                                i+k = const of the (i,k) grid; a set S_{i,k}
                                is one serial chain over ascending j */
 #define CC_SCHED_SUMMOD 1   /* phase s: triplets with (i+j+k) mod n = s */
@@ -116,7 +116,9 @@ typedef struct cc_opts {
                                the violation is <= a = max(tol, refine_at),
                                or is <= 100 a and stops decreasing between
                                checks (FP32's floor; early plateaus of the
-                               violation do not count); default 1e-5 */
+                               violation do not count), then runs
+                               refine_sweeps FP64 sweeps before the
+                               tolerance may end the solve; default 1e-5 */
   int32_t trace;            /* 1: record per-work-item timestamps of each
                                fused tiled sweep (cc_get_trace); default 0 */
   int32_t interleave;       /* tiled schedule: 1 = deal the objects over the
@@ -162,6 +164,16 @@ typedef struct cc_opts {
                                triples / 2)).  A sweep whose next pool overflows
                                is undone and run again with the pool grown to
                                1.5 x the entries it needed. */
+  int32_t refine_sweeps;    /* CC_PREC_FP32_REFINE: FP64 sweeps that follow the
+                               switch to FP64 before cc_solve (or
+                               cc_batch_solve, for that instance) may stop at
+                               the tolerance, >= 1; default 5.  x and f
+                               rebuilt from the FP32 duals carry their
+                               rounding (LP objective about 1e-5 relative
+                               off on the Chung-Lu n = 1000 / 2000
+                               instances); five FP64 sweeps bring the
+                               objective back to within 1e-8 of the FP64
+                               solve's at the same sweep. */
 } cc_opts;
 
 typedef struct cc_stats {
@@ -241,7 +253,10 @@ int cc_set_state(cc_handle* h, const double* x, const double* f, const double* y
  * identity v = v0 - W^{-1} A^T y / eps that Dykstra's method keeps
  * (Algorithm 1), so that FP32 rounding in x does not carry into the
  * refinement.  cc_solve does this by itself when the FP32 state first meets
- * the tolerance.  No-op for FP64 state. */
+ * max(tol, opts.refine_at) (or stalls near it) and then runs
+ * opts.refine_sweeps FP64 sweeps before it checks the tolerance again; after
+ * an explicit call cc_solve also runs those sweeps before it may stop.
+ * No-op for FP64 state. */
 int cc_refine_fp64(cc_handle* h);
 
 /* Warm start: set the duals (y_tri: 3 C(n,3) doubles, y_pair: 2P doubles,
@@ -276,26 +291,32 @@ int64_t cc_device_bytes(const cc_handle* h);
  * when they need the check, e.g. a program whose device memory is reserved
  * in full by another allocator (a framework's pool, a plugin host with a
  * fixed budget), or a latency-critical loop where cudaMalloc/cudaFree may
- * synchronize the whole device.  It computes what cc_check reports, from the
- * caller's own device arrays in the public layouts:
+ * synchronize the whole device.  It computes what cc_check reports for the
+ * CC LP problem (opts.problem = CC_PROB_CC: metric rows, pair rows, and the
+ * objectives of Eq. qp with c = (0, w); for l2 nearness use cc_check, whose
+ * l2 quantities differ), from the caller's own device arrays in the public
+ * layouts:
  *   x, f, d, w   P = n(n-1)/2 doubles each, packed order (device pointers)
  *   y_pair       2P doubles, packed order (device pointer)
  *   out          8 doubles (device pointer, written): max_violation,
  *                pair_violation, lp_objective, wf, qp_primal,
  *                dual_objective, gap, 0
  * and runs asynchronously on `stream` (cudaStream_t; NULL = legacy default
- * stream) on the current device.  It calls no cudaMalloc/cudaFree and no
- * allocating library routine.  Its scratch is a fixed array in the library's
- * device memory of 6 * CC_NOALLOC_MAX_N doubles (192 KB), held on every GPU
- * that loads the library until the process exits; n > CC_NOALLOC_MAX_N is
- * rejected with CC_ERR_ARG.  The first call on a device looks up that
- * array's device address (with the device current) and caches it; make that
- * first call before any stream capture.  All calls share the one array, and
- * each call writes every entry it later reads, so no clearing is needed;
- * calls whose kernels overlap on the GPU (different streams, no ordering)
- * race on it and must be serialized by the caller.  Errors: CC_ERR_ARG (NULL
- * array, n < 3, n > CC_NOALLOC_MAX_N, eps <= 0), CC_ERR_CUDA; the message is
- * in cc_last_error(NULL). */
+ * stream) on the current device.  The work is cut into at most
+ * CC_NOALLOC_MAX_N chunks of equal triplet and pair counts, one CTA each.
+ * It calls no cudaMalloc/cudaFree and no allocating library routine.  Its
+ * scratch is a fixed array in the library's device memory of
+ * 6 * CC_NOALLOC_MAX_N doubles (192 KB), held on every GPU that loads the
+ * library until the process exits; n > CC_NOALLOC_MAX_N is rejected with
+ * CC_ERR_ARG.  The first call on a device looks up that array's device
+ * address (with the device current) and caches it with the identity of the
+ * current context; a call in another context (e.g. after cudaDeviceReset)
+ * looks it up again.  Make the first call on a device before any stream
+ * capture.  All calls share the one array, and each call writes every entry
+ * it later reads, so no clearing is needed; calls whose kernels overlap on
+ * the GPU (different streams, no ordering) race on it and must be serialized
+ * by the caller.  Errors: CC_ERR_ARG (NULL array, n < 3, n > CC_NOALLOC_MAX_N,
+ * eps <= 0), CC_ERR_CUDA; the message is in cc_last_error(NULL). */
 int cc_check_noalloc(int64_t n, double eps, const double* x, const double* f, const double* d,
                      const double* w, const double* y_pair, double* out, void* stream);
 

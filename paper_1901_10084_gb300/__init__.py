@@ -82,7 +82,7 @@ class Solver:
                  exact=False, check_every=10, device=0, stream=None, torch_alloc=True,
                  barrier_timeout_s=2.0, grid=0, debug_skip_cta=-1, on_device=False, variant=0,
                  refine_at=1e-5, trace=False, interleave=True, problem="cc", store="dense",
-                 pool_entries=0):
+                 pool_entries=0, refine_sweeps=5):
         o = cc_opts_default()
         o.problem = PROBLEMS[problem] if isinstance(problem, str) else int(problem)
         o.store = STORES[store] if isinstance(store, str) else int(store)
@@ -99,6 +99,7 @@ class Solver:
         o.debug_skip_cta = int(debug_skip_cta)
         o.variant = int(variant)
         o.refine_at = float(refine_at)
+        o.refine_sweeps = int(refine_sweeps)
         o.trace = 1 if trace else 0
         o.interleave = 1 if interleave else 0
         self._alloc = None
@@ -221,7 +222,8 @@ class Batch:
     a Solver view of instance i (get_x, get_duals, check, set_state ...)."""
 
     def __init__(self, instances, eps=0.2, tile=16, precision="fp64", check_every=10, device=0,
-                 stream=None, torch_alloc=True, interleave=True, batch_order=0, grid=0, variant=0):
+                 stream=None, torch_alloc=True, interleave=True, batch_order=0, grid=0, variant=0,
+                 refine_sweeps=5):
         import torch
         o = cc_opts_default()
         o.eps = float(eps)
@@ -233,6 +235,7 @@ class Batch:
         o.batch_order = int(batch_order)
         o.grid = int(grid)
         o.variant = int(variant)
+        o.refine_sweeps = int(refine_sweeps)
         if stream is None:
             stream = torch.cuda.current_stream(device)
         o.stream = ctypes.c_void_p(int(stream.cuda_stream))

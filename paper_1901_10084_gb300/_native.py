@@ -34,6 +34,8 @@ CC_PROB_L2 = 1
 CC_STORE_DENSE = 0
 CC_STORE_SPARSE = 1
 
+CC_NOALLOC_MAX_N = 4096
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -62,6 +64,7 @@ class cc_opts(ctypes.Structure):
         ("problem", ctypes.c_int32),
         ("store", ctypes.c_int32),
         ("pool_entries", ctypes.c_int64),
+        ("refine_sweeps", ctypes.c_int32),
     ]
 
 

@@ -46,6 +46,7 @@ struct cc_handle {
   double* d64 = nullptr;     // FP64 problem data, kept for the whole solve
   double* winv64 = nullptr;
   int64_t fp32_sweeps = 0;
+  int64_t fp64_from = -1;   // sweep count when the state left FP32 (-1: never in this state)
   void* zt = nullptr;
   void* zp = nullptr;
   int64_t tile_elems = 0;   // ntiles * B * B
@@ -546,24 +547,27 @@ int build_list_tables(cc_handle* h) {
     CK(h, cudaMemcpyAsync(h->l_phoff, phoff.data(), phoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h->st));
     CK(h, cudaStreamSynchronize(h->st));
   } else {
-    // the listing of the sets S_{i,k} (1-based x, z, c as printed; stored 0-based)
+    // the sets S_{i,k} (outer pair i < k - 1, 0-based here) grouped by the
+    // anti-diagonal i + k: the paper's phases are the 1-based sums n+1 down
+    // to 4, then n+2 up to 2n-2, i.e. 0-based sums n-1 down to 2, then n up to
+    // 2n-4; inside a phase ascending i, inside a set ascending j
     std::vector<int> sets, setidx((size_t)n * n, -1);
     std::vector<int64_t> setoff, phoff;
     int64_t run = 0;
-    auto add_phase = [&](int x, int z) {
+    auto add_diagonal = [&](int sum) {
       phoff.push_back((int64_t)sets.size());
-      const int g = (z - x - 2) / 2;
-      for (int c = 0; c <= g; ++c) {
-        const int i = x + c - 1, k = z - c - 1;
+      int units = 0;
+      for (int i = std::max(0, sum - (n - 1)); sum - 2 * i >= 2; ++i, ++units) {
+        const int k = sum - i;
         setidx[(size_t)i * n + k] = (int)sets.size();
         sets.push_back(i | (k << 16));
         setoff.push_back(run);
         run += k - i - 1;
       }
-      h->max_units_phase = std::max<int64_t>(h->max_units_phase, g + 1);
+      h->max_units_phase = std::max<int64_t>(h->max_units_phase, units);
     };
-    for (int z = n; z >= 3; --z) add_phase(1, z);
-    for (int x = 2; x <= n - 2; ++x) add_phase(x, n);
+    for (int sum = n - 1; sum >= 2; --sum) add_diagonal(sum);
+    for (int sum = n; sum <= 2 * n - 4; ++sum) add_diagonal(sum);
     L.nphases = (int)phoff.size();
     phoff.push_back((int64_t)sets.size());
     if (run != h->T3) return fail(h, CC_ERR_ARG, "schedule 0 table does not cover every triplet");
@@ -782,6 +786,7 @@ int check_opts(const cc_opts& o) {
     return fail(nullptr, CC_ERR_UNSUPPORTED, "l2 metric nearness runs in FP64");
   if (o.store != CC_STORE_DENSE && o.store != CC_STORE_SPARSE) return fail(nullptr, CC_ERR_ARG, "unknown store");
   if (o.pool_entries < 0) return fail(nullptr, CC_ERR_ARG, "pool_entries must be >= 0");
+  if (o.refine_sweeps < 1) return fail(nullptr, CC_ERR_ARG, "refine_sweeps must be >= 1");
   if (o.store == CC_STORE_SPARSE &&
       (o.schedule != CC_SCHED_TILED || o.exact || (o.variant != 0 && o.variant != 3 && o.variant != 4)))
     return fail(nullptr, CC_ERR_UNSUPPORTED, "the sparse store runs the tiled schedule, fused form, variant 0, 3 or 4");
@@ -894,6 +899,7 @@ int switch_to_fp64(cc_handle* h) {
   }
   h->fp32 = false;
   h->esz = 8;
+  h->fp64_from = h->sweeps;
   rc = resync_fp64(h);
   if (rc) return rc;
   rc = configure_sweep(h);
@@ -907,6 +913,12 @@ int switch_to_fp64(cc_handle* h) {
     CK(h, cudaMemsetAsync(h->sp_scratch, 0, scratch * sizeof(double), h->st));
   }
   return CC_OK;
+}
+
+// FP64 refinement done: the state never left FP32 in this solve, or has run
+// opts.refine_sweeps FP64 sweeps since it did.
+static bool refined(const cc_handle* h) {
+  return !h->fp32 && (h->fp64_from < 0 || h->sweeps - h->fp64_from >= h->o.refine_sweeps);
 }
 
 // Message for cc_last_error(NULL) from entry points outside this file.
@@ -941,6 +953,7 @@ void cc_opts_default(cc_opts* o) {
   o->problem = CC_PROB_CC;
   o->store = CC_STORE_DENSE;
   o->pool_entries = 0;
+  o->refine_sweeps = 5;
 }
 
 int cc_create_device(cc_handle** out, int64_t n, const double* d_dev, const double* w_dev, const cc_opts* opts) {
@@ -1150,28 +1163,33 @@ int cc_solve(cc_handle* h, double tol, int64_t max_sweeps, int64_t* sweeps_done)
     cc_stats s;
     rc = cc_check(h, &s);
     if (rc) return rc;
-    if (!h->fp32) {
-      // l2 nearness also needs the gap closed: Dykstra's iterate is often
-      // feasible long before it is optimal (gap = sum w x (x - d) >= 0 at the optimum)
-      if (s.max_violation <= tol &&
-          (h->o.problem != CC_PROB_L2 || std::fabs(s.gap) <= tol * std::max(s.qp_primal, 1e-300)))
-        return CC_OK;
-      continue;
-    }
-    // FP32 bulk phase: refine in FP64 (from the converted duals) once the
-    // violation is small enough for FP32, or stops decreasing near that
-    // level (early plateaus of Dykstra's violation are not FP32's floor)
-    const double at = std::max(tol, h->o.refine_at);
-    const bool small = s.max_violation <= at;
-    const bool stalled = s.max_violation <= 100.0 * at && s.max_violation > 0.99 * prev_fp32;
-    prev_fp32 = s.max_violation;
-    if (small || stalled) {
+    if (h->fp32) {
+      // FP32 bulk phase: go to FP64 (duals converted, x and f rebuilt from
+      // them) once the violation is small enough for FP32, or stops
+      // decreasing near that level (early plateaus of Dykstra's violation
+      // are not FP32's floor); then run the refinement sweeps in FP64 at
+      // once: the rebuilt point carries the FP32 duals' rounding (its LP
+      // objective about 1e-5 off), which a few FP64 sweeps remove
+      const double at = std::max(tol, h->o.refine_at);
+      const bool small = s.max_violation <= at;
+      const bool stalled = s.max_violation <= 100.0 * at && s.max_violation > 0.99 * prev_fp32;
+      prev_fp32 = s.max_violation;
+      if (!(small || stalled)) continue;
       rc = switch_to_fp64(h);
       if (rc) return rc;
+      k = std::min<int64_t>(h->o.refine_sweeps, max_sweeps - done);
+      rc = cc_sweep(h, k);
+      if (rc) return rc;
+      done += k;
+      if (sweeps_done) *sweeps_done = done;
       rc = cc_check(h, &s);
       if (rc) return rc;
-      if (s.max_violation <= tol) return CC_OK;
     }
+    // l2 nearness also needs the gap closed: Dykstra's iterate is often
+    // feasible long before it is optimal (gap = sum w x (x - d) >= 0 at the optimum)
+    if (s.max_violation <= tol && refined(h) &&
+        (h->o.problem != CC_PROB_L2 || std::fabs(s.gap) <= tol * std::max(s.qp_primal, 1e-300)))
+      return CC_OK;
   }
   return fail(h, CC_ERR_NOT_CONVERGED, "max_sweeps reached before the tolerance");
 }
@@ -1315,6 +1333,7 @@ int cc_set_state(cc_handle* h, const double* x, const double* f, const double* y
     CK(h, cudaStreamSynchronize(h->st));
   }
   h->sweeps = 0;
+  h->fp64_from = -1;   // a state set by the caller needs no refinement sweeps
   h->fresh = false;
   return CC_OK;
 }
@@ -1344,6 +1363,7 @@ int cc_set_duals(cc_handle* h, const double* y_tri, const double* y_pair) {
   rc = resync_fp64(h);
   if (rc) return rc;
   h->sweeps = 0;
+  h->fp64_from = -1;   // a state set by the caller needs no refinement sweeps
   h->fresh = false;
   h->fp32_sweeps = 0;
   return CC_OK;
@@ -1674,13 +1694,12 @@ int cc_batch_solve(cc_batch* b, double tol, int64_t max_sweeps, int64_t* sweeps_
         const bool stalled = s.max_violation <= 100.0 * at && s.max_violation > 0.99 * b->prev_fp32[i];
         b->prev_fp32[i] = s.max_violation;
         if (!(small || stalled)) continue;
-        rc = switch_to_fp64(h);
+        rc = switch_to_fp64(h);   // its FP64 refinement sweeps come with the next batch sweeps
         if (rc) return bfail(b, rc, h->err);
         b->stale[0] = b->stale[1] = true;
-        rc = cc_check(h, &s);
-        if (rc) return bfail(b, rc, h->err);
+        continue;
       }
-      if (s.max_violation <= tol) {
+      if (s.max_violation <= tol && refined(h)) {
         b->active[i] = 0;
         b->stale[0] = b->stale[1] = true;
         --left;
@@ -1924,6 +1943,7 @@ int cc_warm_start_mlp(cc_handle* h, const float* params, double threshold, int64
   ws_release(h, c);
   if (rc) return rc;
   h->sweeps = 0;
+  h->fp64_from = -1;   // a state set by the caller needs no refinement sweeps
   h->fresh = false;
   h->fp32_sweeps = 0;
   if (candidates) *candidates = c.count;

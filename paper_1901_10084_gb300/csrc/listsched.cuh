@@ -9,7 +9,8 @@
 // n x (n+1) table, no triplet list), the middle index from the at most three
 // runs of j with i+j+k = s, s+n, s+2n.  Duals: phase-major, 3 per triplet.
 //
-// Schedule 0 (the paper's diagonal listing of the sets S_{i,k}): one thread
+// Schedule 0 (the paper's diagonal schedule: the sets S_{i,k}, one phase per
+// anti-diagonal i + k of the (i, k) grid): one thread
 // per set; the set's triplets run serially in ascending j, carrying x_ik in a
 // register.  Duals: set by set in schedule order, 3 per triplet.
 #pragma once

@@ -6,10 +6,14 @@
 // allocator (a framework's memory pool, a fixed-budget plugin host), or a
 // latency-critical loop where cudaMalloc/cudaFree may synchronize the whole
 // device.  This entry point reads the caller's arrays, writes the caller's
-// output array, and keeps its only scratch (one partial result per object) in
-// a fixed array in the library's own device memory, so it allocates nothing.
+// output array, and keeps its only scratch (the partial results of at most
+// CC_NOALLOC_MAX_N equal chunks of the work) in a fixed array in the
+// library's own device memory, so it allocates nothing.  It serves the CC LP
+// problem (metric rows, pair rows and the objectives of Eq. qp with
+// c = (0, w)); l2 nearness handles report through cc_check.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -17,19 +21,53 @@
 
 namespace {
 
-// Six partial results per object: metric violation max, pair violation max,
-// sum w|x-d|, sum w f, sum w (x^2 + f^2), sum d (y+ - y-).  Every GPU that
-// loads the library holds this array (6 * CC_NOALLOC_MAX_N doubles) until
-// the process exits.
+// Six partial results per chunk of work: metric violation max, pair violation
+// max, sum w|x-d|, sum w f, sum w (x^2 + f^2), sum d (y+ - y-).  Every GPU
+// that loads the library holds this array (6 * CC_NOALLOC_MAX_N doubles)
+// until the process exits.  A call cuts its work into at most
+// CC_NOALLOC_MAX_N chunks, one CTA each, and uses one column per chunk.
 constexpr int kParts = 6;
-static __device__ __align__(256) double g_noalloc_scratch[kParts * CC_NOALLOC_MAX_N];
+constexpr int kSlots = CC_NOALLOC_MAX_N;
+constexpr int kThreads = 256;
+constexpr int64_t kMinTripletsPerChunk = 1 << 16;
+static __device__ __align__(256) double g_noalloc_scratch[kParts * kSlots];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-double* g_scratch_addr[kMaxDevices] = {};
+struct ScratchSlot {
+  double* addr;
+  unsigned long long ctx_id;   // context the address belongs to (0: unknown)
+};
+ScratchSlot g_scratch[kMaxDevices] = {};
 
 __host__ __device__ inline int64_t packed(int64_t n, int64_t i, int64_t j) {
   return i * n - i * (i + 1) / 2 + (j - i - 1);
+}
+__host__ __device__ inline int64_t choose2(int64_t m) { return m < 2 ? 0 : m * (m - 1) / 2; }
+__host__ __device__ inline int64_t choose3(int64_t m) { return m < 3 ? 0 : m * (m - 1) * (m - 2) / 6; }
+
+// First triplet (i, j, k), i < j < k, of lexicographic rank r among the
+// triplets of {0..n-1}: i is the largest index whose earlier first indices
+// hold at most r triplets, j likewise inside i's block, then k.
+__device__ inline void unrank_triplet(int64_t n, int64_t r, int64_t& i, int64_t& j, int64_t& k) {
+  const int64_t T = choose3(n);
+  int64_t lo = 0, hi = n - 3;
+  while (lo < hi) {   // triplets with first index < i: T - C(n - i, 3)
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (T - choose3(n - mid) <= r) lo = mid; else hi = mid - 1;
+  }
+  i = lo;
+  int64_t q = r - (T - choose3(n - i));
+  const int64_t m = n - 1 - i;     // objects after i; pairs (j, k) among them
+  lo = 0;
+  hi = m - 2;
+  while (lo < hi) {   // pairs with local first index < a: C(m, 2) - C(m - a, 2)
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (choose2(m) - choose2(m - mid) <= q) lo = mid; else hi = mid - 1;
+  }
+  j = i + 1 + lo;
+  q -= choose2(m) - choose2(m - lo);
+  k = j + 1 + q;
 }
 
 __device__ inline double warp_max(double v) {
@@ -41,34 +79,58 @@ __device__ inline double warp_sum(double v) {
   return v;
 }
 
-// One CTA per object i: the violation of every triplet whose smallest index
-// is i, and the pair terms of the pairs (i, j > i).  Writes the six partials
-// of row i; the final step reads exactly the rows 0..n-1 written here.
-__global__ void __launch_bounds__(256) k_noalloc_rows(int n, const double* __restrict__ x,
-                                                     const double* __restrict__ f,
-                                                     const double* __restrict__ d,
-                                                     const double* __restrict__ w,
-                                                     const double* __restrict__ yp, double* scratch) {
-  const int i = blockIdx.x;
-  __shared__ double red[kParts][8];
-  double mv = 0.0, pv = 0.0, lp = 0.0, wf = 0.0, quad = 0.0, by = 0.0;
-  const int64_t m = n - 1 - i;                   // objects j > i
-  const int64_t pairs_jk = m * (m - 1) / 2;      // (j, k) with i < j < k
-  for (int64_t q = threadIdx.x; q < pairs_jk; q += blockDim.x) {
-    // q-th pair (j, k) of the objects i+1..n-1, row-major
-    int64_t lo = 0, hi = m - 2;
-    while (lo < hi) {
-      int64_t mid = (lo + hi + 1) >> 1;
-      if (mid * m - mid * (mid + 1) / 2 <= q) lo = mid; else hi = mid - 1;
-    }
-    const int64_t j = i + 1 + lo;
-    const int64_t k = j + 1 + (q - (lo * m - lo * (lo + 1) / 2));
-    const double xij = x[packed(n, i, j)], xik = x[packed(n, i, k)], xjk = x[packed(n, j, k)];
-    const double v0 = (xij - xik) - xjk, v1 = (xik - xij) - xjk, v2 = (xjk - xij) - xik;
-    mv = fmax(mv, fmax(v0, fmax(v1, v2)));
+// CTA b of `chunks`: the triplets of lexicographic ranks [b T / chunks,
+// (b+1) T / chunks) and the pairs [b P / chunks, (b+1) P / chunks), so every
+// CTA gets the same amount of work whatever n.  The triplets of a chunk form
+// runs of consecutive k for fixed (i, j) (a row); the warps take the rows in
+// turn and their lanes consecutive k, so the reads of x_ik and x_jk are
+// contiguous.  Writes the six partials of column b; the final step reads
+// exactly the columns 0..chunks-1 written by this launch.
+__global__ void __launch_bounds__(kThreads) k_noalloc_chunks(int n, int chunks, const double* __restrict__ x,
+                                                            const double* __restrict__ f,
+                                                            const double* __restrict__ d,
+                                                            const double* __restrict__ w,
+                                                            const double* __restrict__ yp, double* scratch) {
+  constexpr int NW = kThreads / 32;
+  __shared__ double red[kParts][NW];
+  __shared__ long long start[3];
+  const int b = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t T = choose3(n), P = choose2(n);
+  const int64_t r0 = T * b / chunks, r1 = T * (b + 1) / chunks;
+  if (threadIdx.x == 0 && r1 > r0) {
+    int64_t i, j, k;
+    unrank_triplet(n, r0, i, j, k);
+    start[0] = i;
+    start[1] = j;
+    start[2] = k;
   }
-  for (int64_t j = i + 1 + threadIdx.x; j < n; j += blockDim.x) {
-    const int64_t p = packed(n, i, j);
+  __syncthreads();
+  double mv = 0.0, pv = 0.0, lp = 0.0, wf = 0.0, quad = 0.0, by = 0.0;
+  if (r1 > r0) {
+    int64_t i = start[0], j = start[1], k0 = start[2], left = r1 - r0;
+    for (int64_t row = 0; left > 0; ++row) {
+      const int64_t len = min(left, (int64_t)n - k0);   // k = k0 .. k0 + len - 1 of row (i, j)
+      if (len <= 0) break;                               // not reached: r1 <= T
+      if (row % NW == wid) {
+        const double xij = x[packed(n, i, j)];
+        const double* xi = x + packed(n, i, k0);   // x_ik for consecutive k are consecutive
+        const double* xj = x + packed(n, j, k0);
+        for (int64_t t = lane; t < len; t += 32) {
+          const double xik = xi[t], xjk = xj[t];
+          const double v0 = (xij - xik) - xjk, v1 = (xik - xij) - xjk, v2 = (xjk - xij) - xik;
+          mv = fmax(mv, fmax(v0, fmax(v1, v2)));
+        }
+      }
+      left -= len;
+      if (++j == n - 1) {   // next row: (i, j + 1), or the first row of i + 1
+        ++i;
+        j = i + 1;
+      }
+      k0 = j + 1;
+    }
+  }
+  for (int64_t p = P * b / chunks + threadIdx.x; p < P * (b + 1) / chunks; p += kThreads) {
     const double xv = x[p], fv = f[p], dv = d[p], wv = w[p];
     lp += wv * fabs(xv - dv);
     wf += wv * fv;
@@ -82,7 +144,6 @@ __global__ void __launch_bounds__(256) k_noalloc_rows(int n, const double* __res
   wf = warp_sum(wf);
   quad = warp_sum(quad);
   by = warp_sum(by);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
     red[0][wid] = mv;
     red[1][wid] = pv;
@@ -94,23 +155,24 @@ __global__ void __launch_bounds__(256) k_noalloc_rows(int n, const double* __res
   __syncthreads();
   if (threadIdx.x < kParts) {
     const int r = threadIdx.x;
-    const int nw = blockDim.x >> 5;
     double v = red[r][0];
-    for (int t = 1; t < nw; ++t) v = (r < 2) ? fmax(v, red[r][t]) : v + red[r][t];
-    scratch[(int64_t)r * CC_NOALLOC_MAX_N + i] = v;
+    for (int t = 1; t < NW; ++t) v = (r < 2) ? fmax(v, red[r][t]) : v + red[r][t];
+    scratch[(int64_t)r * kSlots + b] = v;
   }
 }
 
-// Single CTA: fold the n row partials in a fixed order and write
-// out[0..7] = {max_violation, pair_violation, lp_objective, wf, qp_primal,
-//              dual_objective, gap, 0}.
-__global__ void __launch_bounds__(256) k_noalloc_final(int n, double eps, const double* scratch, double* out) {
-  __shared__ double red[kParts][8];
+// Single CTA: fold the partials of the `chunks` columns in a fixed order and
+// write out[0..7] = {max_violation, pair_violation, lp_objective, wf,
+// qp_primal, dual_objective, gap, 0}.
+__global__ void __launch_bounds__(kThreads) k_noalloc_final(int chunks, double eps, const double* scratch,
+                                                           double* out) {
+  constexpr int NW = kThreads / 32;
+  __shared__ double red[kParts][NW];
   double acc[kParts];
   for (int r = 0; r < kParts; ++r) acc[r] = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int c = threadIdx.x; c < chunks; c += kThreads) {
     for (int r = 0; r < kParts; ++r) {
-      const double v = scratch[(int64_t)r * CC_NOALLOC_MAX_N + i];
+      const double v = scratch[(int64_t)r * kSlots + c];
       acc[r] = (r < 2) ? fmax(acc[r], v) : acc[r] + v;
     }
   }
@@ -121,11 +183,10 @@ __global__ void __launch_bounds__(256) k_noalloc_final(int n, double eps, const 
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const int nw = blockDim.x >> 5;
     double v[kParts];
     for (int r = 0; r < kParts; ++r) {
       v[r] = red[r][0];
-      for (int t = 1; t < nw; ++t) v[r] = (r < 2) ? fmax(v[r], red[r][t]) : v[r] + red[r][t];
+      for (int t = 1; t < NW; ++t) v[r] = (r < 2) ? fmax(v[r], red[r][t]) : v[r] + red[r][t];
     }
     const double qp = v[3] + 0.5 * eps * v[4];
     const double dual = -v[5] - 0.5 * eps * v[4];
@@ -140,21 +201,55 @@ __global__ void __launch_bounds__(256) k_noalloc_final(int n, double eps, const 
   }
 }
 
-// Address of the scratch array on the current device, looked up once per
-// device (with that device current) and cached.
+// Identifier of the current context (cuCtxGetId through the runtime's driver
+// entry-point lookup, so the library needs no link against the driver
+// library); 0 when there is no current context or the driver lacks the call.
+unsigned long long current_context_id() {
+  using GetCurrent = int (*)(void**);
+  using GetId = int (*)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(p);
+  });
+  if (!get_current || !get_id) return 0;
+  void* ctx = nullptr;
+  if (get_current(&ctx) != 0 || !ctx) return 0;
+  unsigned long long id = 0;
+  return get_id(ctx, &id) == 0 ? id : 0;
+}
+
+// Address of the scratch array in the current device's context.  The set-up
+// (cudaGetSymbolAddress, with the device current) runs on the first call on
+// a device, and again only when that device's current context differs from
+// the one the address was taken in (after cudaDeviceReset the module is
+// loaded anew and the array may move).  Where the context cannot be
+// identified the address is looked up on every call.
 cudaError_t scratch_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
+  ScratchSlot& slot = g_scratch[dev];
+  const unsigned long long id = current_context_id();
+  if (!slot.addr || id == 0 || id != slot.ctx_id) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = static_cast<double*>(p);
+    slot.addr = static_cast<double*>(p);
+    slot.ctx_id = id ? id : current_context_id();   // the lookup made the primary context current
   }
-  *out = g_scratch_addr[dev];
+  *out = slot.addr;
   return cudaSuccess;
 }
 
@@ -189,8 +284,10 @@ extern "C" int cc_check_noalloc(int64_t n, double eps, const double* x, const do
     return CC_ERR_CUDA;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  k_noalloc_rows<<<(unsigned)n, 256, 0, st>>>((int)n, x, f, d, w, y_pair, scratch);
-  k_noalloc_final<<<1, 256, 0, st>>>((int)n, eps, scratch, out);
+  const int64_t per = kMinTripletsPerChunk;
+  const int chunks = (int)std::min<int64_t>(kSlots, std::max<int64_t>(1, (choose3(n) + per - 1) / per));
+  k_noalloc_chunks<<<(unsigned)chunks, kThreads, 0, st>>>((int)n, chunks, x, f, d, w, y_pair, scratch);
+  k_noalloc_final<<<1, kThreads, 0, st>>>(chunks, eps, scratch, out);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     ccd_set_global_error(cudaGetErrorString(e));

@@ -553,16 +553,18 @@ __device__ __forceinline__ int flow_subphases(const TiledArgs<T>& a, int w, Flow
           if (differs(z0, o0)) st_stream(zs + slot, z0);
           if (differs(z1, o1)) st_stream(zs + C::BB + slot, z1);
           if (differs(z2, o2)) st_stream(zs + 2 * C::BB + slot, z2);
+          // a dual that became zero or nonzero flips its bit in the item's
+          // shared-memory mask, written back once at the end of the item
+          // (the words of sub-phase t belong to one warp and are read only
+          // at the top of sub-phase t, before any flip)
+          uint32_t* mw = a.sparse ? sm.nmask : sm.mask;
+          const uint32_t bit = 1u << lane;
+          const bool f0 = nz(z0) != b0, f1 = nz(z1) != b1, f2 = nz(z2) != b2;
+          if (f0) atomicXor(&mw[q0], bit);
+          if (f1) atomicXor(&mw[q1], bit);
+          if (f2) atomicXor(&mw[q2], bit);
+          if ((f0 | f1 | f2) && !a.sparse) sm.dirty = 1;
           touched = 1;
-        }
-        const uint32_t n0 = __ballot_sync(0xffffffffu, need ? nz(z0) : b0);
-        const uint32_t n1 = __ballot_sync(0xffffffffu, need ? nz(z1) : b1);
-        const uint32_t n2 = __ballot_sync(0xffffffffu, need ? nz(z2) : b2);
-        if (lane == 0) {
-          uint32_t* mw = a.sparse ? sm.nmask : a.mask + (int64_t)w * M::PER_BT;
-          if (n0 != m0) mw[q0] = n0;
-          if (n1 != m1) mw[q1] = n1;
-          if (n2 != m2) mw[q2] = n2;
         }
       }
     }
@@ -889,7 +891,7 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
   bool any_touched;
   if constexpr (WARP) any_touched = __any_sync(0xffffffffu, touched);
   else any_touched = __syncthreads_or(touched);
-  if (!WARP && SHADOW && sm.dirty && !a.sparse) {
+  if (sm.dirty && !a.sparse) {   // the item's mask words, once, if any bit flipped
     uint32_t* mw = a.mask + (int64_t)w * M::PER_BT;
     for (int e = tid; e < M::PER_BT; e += NTH) mw[e] = sm.mask[e];
   }

@@ -43,6 +43,41 @@ def init_params(seed: int = 0, out_bias: float = -3.0) -> np.ndarray:
     return np.concatenate([a.ravel() for a in parts]).astype(np.float32)
 
 
+def dpattern_constant(feat: torch.Tensor, target: torch.Tensor):
+    """Mean training dual of the rows a cold start violates first: the row
+    whose hypotenuse is the only non-edge (d = 1) of a triplet whose other
+    two pairs are edges (d = 0).  Returns (constant, number of such rows)."""
+    dv = feat[:, :3]
+    tot, cnt = 0.0, 0
+    for r in range(3):
+        legs = [q for q in range(3) if q != r]
+        m = (dv[:, r] == 1) & (dv[:, legs[0]] == 0) & (dv[:, legs[1]] == 0)
+        cnt += int(m.sum())
+        tot += float(target[m, r].double().sum())
+    return (tot / cnt if cnt else 0.0), cnt
+
+
+def dpattern_params(c: float, off: float = -12.0) -> np.ndarray:
+    """Network parameters that compute the trivial d-pattern predictor on the
+    same inference path: hidden unit r = relu(d_r - d_a - d_b), which is 1
+    exactly on the pattern of ``dpattern_constant`` for row r (d in {0, 1})
+    and 0 otherwise, carried through layer 2 unchanged; output r =
+    softplus(a h_r + off) with a chosen so that the pattern gives about c
+    (BF16 rounding of a moves it by under 5 %) and the rest softplus(off),
+    about 6e-6, which any threshold above it sets to 0."""
+    W1, b1, W2, b2, W3, b3 = [np.zeros_like(a) for a in unpack(np.zeros(CC_WS_NPARAM, dtype=np.float32))]
+    for r in range(3):
+        W1[:, r] = 0.0
+        W1[r, r] = 1.0
+        for q in range(3):
+            if q != r:
+                W1[q, r] = -1.0
+        W2[r, r] = 1.0
+        W3[r, r] = (np.log(np.expm1(c)) - off) if c > 0 else 0.0
+    b3[:] = off
+    return np.concatenate([a.ravel() for a in (W1, b1, W2, b2, W3, b3)]).astype(np.float32)
+
+
 def samples(solver, device=None):
     """(features, targets) of a solver's current state as device tensors of
     shape (m, CC_WS_FEAT) and (m, 3)."""

@@ -37,12 +37,13 @@ def test_opts_defaults(lib):
     o = N.cc_opts_default()
     assert o.eps == 0.2 and o.schedule == N.CC_SCHED_TILED and o.tile == 16
     assert o.precision == N.CC_PREC_FP64 and o.check_every == 10 and o.debug_skip_cta == -1
+    assert o.refine_sweeps == 5 and o.refine_at == 1e-5
 
 
 @pytest.mark.parametrize("field,value", [("eps", 0.0), ("eps", -1.0), ("eps", float("inf")),
                                          ("tile", 12), ("check_every", 0),
                                          ("barrier_timeout_s", 0.0), ("precision", 7), ("variant", 5),
-                                         ("variant", -1)])
+                                         ("variant", -1), ("refine_sweeps", 0), ("refine_sweeps", -3)])
 def test_bad_options_rejected_before_device_work(lib, field, value):
     import numpy as np
     from paper_1901_10084_gb300 import _native as N
@@ -98,6 +99,7 @@ def test_warm_start_parameter_count_matches_the_network():
     assert re.search(r"#define CC_WS_NPARAM %d\b" % N.CC_WS_NPARAM, src)
     assert re.search(r"#define CC_WS_FEAT %d\b" % N.CC_WS_FEAT, src)
     assert re.search(r"#define CC_WS_PAIR_PASSES %d\b" % N.CC_WS_PAIR_PASSES, src)
+    assert re.search(r"#define CC_NOALLOC_MAX_N %d\b" % N.CC_NOALLOC_MAX_N, src)
     p = warmstart.init_params(0)
     assert p.shape == (N.CC_WS_NPARAM,) and p.dtype.name == "float32"
     W1, b1, W2, b2, W3, b3 = warmstart.unpack(p)

@@ -61,6 +61,7 @@ def test_batch_solve_matches_single_solves(precision):
                 assert _rel(x, x1) <= 1e-12      # same order, same arithmetic
             else:
                 assert np.max(np.abs(x - x1)) <= 1e-4
+                assert 0 < st["fp32_sweeps"] <= per[i] - 5   # refinement sweeps ran in FP64
 
 
 def test_autotuner_returns_a_valid_choice():

@@ -73,7 +73,7 @@ def test_exact_mode_is_bitwise_equal(n, tile, weighted):
 @pytest.mark.parametrize("schedule", [0, 1])
 @pytest.mark.parametrize("n,weighted", [(60, False), (61, True), (3, False), (4, True), (33, False)])
 def test_paper_schedules_exact_bitwise(schedule, n, weighted):
-    """Schedules 0 (the paper's diagonal listing) and 1 (sum mod n) on the
+    """Schedules 0 (the paper's diagonal schedule) and 1 (sum mod n) on the
     GPU, row by row as Algorithm 1 states it: bit-identical to the oracle."""
     d, w, _ = planted_partition(n, 3, 0.8, 0.1, seed=n, weights=(0.5, 2.0) if weighted else None)
     o = oracle.State(n, d, w, 0.2)
@@ -310,6 +310,23 @@ def test_barrier_time_limit_reports_and_context_survives():
         _assert_state_equal(_gpu_state(s), o)
 
 
+@pytest.mark.parametrize("n,tile,weighted", [(300, 16, True), (217, 8, False)])
+def test_one_sweep_late_in_the_solve(n, tile, weighted):
+    """One GPU sweep from an oracle state 60 sweeps into the solve, where most
+    rows carry nonzero duals and the row-skip filters decide differently than
+    in the first sweeps: x, f and all duals within 1e-12 per sweep."""
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=n + 3, weights=(0.5, 2.0) if weighted else None)
+    o = oracle.State(n, d, w, 0.2)
+    for _ in range(60):
+        o.sweep(2, tile)
+    assert np.count_nonzero(o.ytri) > 1000
+    with _solver(n, d, w, eps=0.2, tile=tile) as s:
+        s.set_state(o.x, o.f, o.ytri, o.ypair)
+        s.sweep(1)
+        o.sweep(2, tile)
+        _assert_state_close(_gpu_state(s), o, TOL_SWEEP)
+
+
 # ---------------------------------------------------------------- full size
 
 def _caller_triplets(n, first, count):
@@ -419,3 +436,85 @@ def test_random_configurations_track_the_oracle():
         else:
             for u, v in zip(g, (o.x, o.f, o.ytri, o.ypair)):
                 assert _rel(u, v) <= 1e-11, what
+
+
+def test_full_size_chunglu1000_converged():
+    """The benchmark workload solved to convergence on both sides (the
+    convergence criteria of Sec. IV-D read as max metric violation <= 1e-4,
+    checked every 10 sweeps): the GPU in the launch configuration bench.py
+    times (FP64, tile 16, relabeled objects, default sweep form) and the
+    oracle's threaded sweep (bit for bit its serial sweep) on the relabeled
+    instance.  Same sweep count, LP objective within 1e-6 relative, x within
+    1e-7 (rounding of the fused form only, over the whole solve)."""
+    import os
+    from relabel import deal_labels
+    n, d, w, _ = workload("chunglu1000")
+    B, tol, every = 16, 1e-4, 10
+    lab = deal_labels(n, B)
+    iu, ju = np.triu_indices(n, 1)
+    a, b = lab[iu], lab[ju]
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    pmap = lo * n - lo * (lo + 1) // 2 + (hi - lo - 1)
+    dint, wint = np.empty_like(d), np.empty_like(w)
+    dint[pmap], wint[pmap] = d, w
+    cores = len(os.sched_getaffinity(0))
+    o = oracle.State(n, dint, wint, 0.2)
+    ko = -1
+    for k in range(1, 1001):
+        o.sweep_threads(2, B, cores)
+        if k % every == 0 and oracle.max_violation(n, o.x, threads=cores) <= tol:
+            ko = k
+            break
+    assert ko > 0
+    with _solver(n, d, w, eps=0.2, tile=B, interleave=True, check_every=every) as s:
+        conv, kg = s.solve(tol, 1000)
+        st = s.check()
+        x, _ = s.get_x()
+    assert conv and kg == ko and st["max_violation"] <= tol
+    oo = o.objectives()
+    assert abs(st["lp_objective"] - oo["lp"]) <= 1e-6 * abs(oo["lp"])
+    assert abs(st["qp_primal"] - oo["qp_primal"]) <= 1e-6 * abs(oo["qp_primal"])
+    assert np.max(np.abs(x - o.x[pmap])) <= 1e-7
+
+
+def test_full_size_chunglu3000w_two_sweeps_sampled():
+    """The precision form's instance (Chung-Lu n = 3000, mean degree 10,
+    w ~ U[0.5, 2]) in FP64 on the dense store, in the launch configuration
+    bench.py times: two sweeps from the start (the first moves only the pair
+    rows, so the second is one sweep from an identical state) against the
+    oracle's threaded sweep on the relabeled instance; x and f in full, the
+    duals on three sampled ranges of 40000 triplets."""
+    import os
+    from relabel import deal_labels
+    n, d, w, _ = workload("chunglu3000w")
+    B = 16
+    lab = deal_labels(n, B)
+    iu, ju = np.triu_indices(n, 1)
+    a, b = lab[iu], lab[ju]
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    pmap = lo * n - lo * (lo + 1) // 2 + (hi - lo - 1)
+    del iu, ju, a, b, lo, hi
+    dint, wint = np.empty_like(d), np.empty_like(w)
+    dint[pmap], wint[pmap] = d, w
+    cores = len(os.sched_getaffinity(0))
+    o = oracle.State(n, dint, wint, 0.2)
+    for _ in range(2):
+        o.sweep_threads(2, B, cores)
+    with _solver(n, d, w, eps=0.2, tile=B, interleave=True) as s:
+        s.sweep(2)
+        x, f = s.get_x()
+        assert _rel(x, o.x[pmap]) <= TOL_SWEEP and _rel(f, o.f[pmap]) <= TOL_SWEEP
+        T = n * (n - 1) * (n - 2) // 6
+        for first in (0, T // 3, T - 40000):
+            yt, _ = s.get_duals(first, 40000, pairs=False)
+            ref = np.empty(3 * 40000)
+            for q, (i, j, k) in enumerate(_caller_triplets(n, first, 40000)):
+                li, lj, lk = lab[i], lab[j], lab[k]
+                u, z = min(li, lj, lk), max(li, lj, lk)
+                v = li + lj + lk - u - z
+                base = 3 * oracle.trank(n, u, v, z)
+                for row, out in enumerate((lk, lj, li)):
+                    ref[3 * q + row] = o.ytri[base + (0 if out == z else 1 if out == v else 2)]
+            assert _rel(yt, ref) <= TOL_SWEEP
+        st = s.check()
+    assert st["max_violation"] == pytest.approx(oracle.max_violation(n, o.x, threads=cores), abs=1e-12)

@@ -85,6 +85,43 @@ def test_fp32_refine_reaches_the_fp64_solution(name, tile):
     assert np.max(np.abs(xb - xa)) <= 1e-5
 
 
+@pytest.mark.parametrize("name,check_every", [("chunglu1000", 10), ("chunglu1000", 5), ("chunglu300", 10)])
+def test_fp32_refine_meets_the_fp64_objective_at_the_solve_tolerance(name, check_every):
+    """The precision form's target at the tolerance the solve is run to
+    (violation 1e-4): the FP32 bulk sweeps end at that tolerance, the
+    refinement then runs opts.refine_sweeps (5) FP64 sweeps from x and f
+    rebuilt out of the converted duals, and the LP objective of the result is
+    within 1e-6 relative of the plain FP64 solve's; the violation meets the
+    tolerance in FP64."""
+    n, d, w, _ = workload(name)
+    res = {}
+    for prec in ("fp64", "fp32_refine"):
+        with _solver(n, d, w, tile=16, precision=prec, check_every=check_every, interleave=True) as s:
+            conv, k = s.solve(1e-4, 3000)
+            st = s.check()
+            res[prec] = (conv, k, st, s.get_x()[0])
+    conv64, k64, s64, x64 = res["fp64"]
+    conv32, k32, s32, x32 = res["fp32_refine"]
+    assert conv64 and conv32
+    assert s32["state_fp32"] == 0 and s32["max_violation"] <= 1e-4
+    assert 0 < s32["fp32_sweeps"] and k32 - s32["fp32_sweeps"] >= 5
+    assert abs(s32["lp_objective"] - s64["lp_objective"]) <= 1e-6 * abs(s64["lp_objective"])
+    assert np.max(np.abs(x32 - x64)) <= 1e-3
+
+
+def test_refinement_sweeps_follow_an_explicit_switch():
+    """After cc_refine_fp64 the solve runs refine_sweeps FP64 sweeps before the
+    tolerance may end it, even when the rebuilt state already meets it."""
+    n, d, w, _ = workload("planted60")
+    with _solver(n, d, w, tile=16, precision="fp32_refine", check_every=1, refine_sweeps=3) as s:
+        s.sweep(200)
+        s.refine_fp64()
+        assert s.check()["max_violation"] <= 1e-3
+        ok, k = s.solve(1e-3, 100)
+        assert ok and k == 3
+        assert s.stats()["sweeps"] - s.stats()["fp32_sweeps"] == 3
+
+
 def test_refine_switch_keeps_the_invariant():
     n = 120
     d, w, _ = chung_lu(n, 2.5, 8.0, seed=4, weights=(0.5, 2.0))

@@ -173,3 +173,62 @@ def test_sparse_store_in_the_fp32_bulk_form(n, tile, weighted, interleave):
             np.testing.assert_array_equal(p, q)
     assert out[0][3][:3] == out[1][3][:3] and out[0][3][0]
     np.testing.assert_array_equal(out[0][3][3], out[1][3][3])
+
+
+# ------------------------------------------------------------- against the oracle
+
+SPARSE_ORACLE_CASES = [(61, 8, False, 5), (61, 16, True, 12), (61, 32, True, 20), (97, 16, True, 20),
+                       (150, 32, False, 8)]
+
+
+@pytest.mark.parametrize("n,tile,weighted,sweeps", SPARSE_ORACLE_CASES)
+def test_sparse_store_matches_the_oracle_over_many_sweeps(n, tile, weighted, sweeps):
+    """The sparse store's own staging, gather and pool code against the
+    oracle (schedule 2 on consecutive blocks, the order the handle walks with
+    interleave off): after `sweeps` sweeps from the start, x, f, every
+    triangle dual (canonical order) and every pair dual element by element.
+    The fused row form differs from the oracle's row only in rounding, so the
+    states agree to rounding level (1e-11 in ||.||_inf / max(||.||_inf, 1)
+    after up to 20 sweeps, as for the dense store); the support of the duals
+    (which duals are nonzero) is compared exactly where the oracle's duals
+    are away from zero."""
+    import oracle
+    import paper_1901_10084_gb300 as cc
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=n + tile, weights=(0.5, 2.0) if weighted else None)
+    o = oracle.State(n, d, w, 0.2)
+    for _ in range(sweeps):
+        o.sweep(2, tile)
+    with cc.Solver(n, d, w, eps=0.2, tile=tile, store="sparse", interleave=False, pool_entries=256) as s:
+        s.sweep(sweeps)
+        x, f = s.get_x()
+        yt, yp = s.get_duals()
+        st = s.stats()
+    rel = lambda a, b: float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1.0))
+    assert rel(x, o.x) <= 1e-11 and rel(f, o.f) <= 1e-11
+    assert rel(yt, o.ytri) <= 1e-11 and rel(yp, o.ypair) <= 1e-11
+    away = np.abs(o.ytri) > 1e-9
+    assert np.array_equal(yt[away] != 0, np.ones(int(away.sum()), dtype=bool))
+    assert st["dual_nnz"] == int(np.count_nonzero(yt))
+    assert np.count_nonzero(o.ytri) > 0
+
+
+def test_sparse_store_late_solve_matches_the_oracle():
+    """Late in the solve, where most nonzero duals sit and the row-skip
+    filters decide differently than early on: 60 sweeps of the sparse store
+    and of the oracle from the start (n = 200, weighted, tile 16), then the
+    state element by element."""
+    import oracle
+    import paper_1901_10084_gb300 as cc
+    n = 200
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=77, weights=(0.5, 2.0))
+    o = oracle.State(n, d, w, 0.2)
+    for _ in range(60):
+        o.sweep(2, 16)
+    with cc.Solver(n, d, w, eps=0.2, tile=16, store="sparse", interleave=False) as s:
+        s.sweep(60)
+        x, f = s.get_x()
+        yt, yp = s.get_duals()
+    rel = lambda a, b: float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1.0))
+    assert rel(x, o.x) <= 1e-10 and rel(f, o.f) <= 1e-10
+    assert rel(yt, o.ytri) <= 1e-10 and rel(yp, o.ypair) <= 1e-10
+    assert np.count_nonzero(o.ytri) > 1000
