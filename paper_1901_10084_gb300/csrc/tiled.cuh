@@ -451,6 +451,103 @@ __device__ __forceinline__ void item_sync() {
   else __syncthreads();
 }
 
+// Barrier of the NTHG threads staging an item: the whole item group
+// (CTA or warp), or, with NAMED, warps 1.. of the CTA on named barrier 1
+// while warp 0 waits for the item's tiles.
+template <int NTHG, bool NAMED>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (NAMED) asm volatile("bar.sync 1, %0;" ::"n"(NTHG) : "memory");
+  else item_sync<NTHG == 32>();
+}
+
+// The item's staging plan from its nonzero-dual bits (sm.mask, loaded):
+// exclusive prefix of the word popcounts (the staging slot of every nonzero
+// dual, sm.pre), the count (sm.total) and, when they fit, asynchronous copies
+// of the nonzero duals of the dense store into sm.dual (or, for the sparse
+// store, the starting copy of the item's new bits).  Run by the NTHG threads
+// of a group, thread gtid; returns the count.  The dual copies are in flight
+// on return.
+template <typename T, int B, int NTHG, bool NAMED>
+__device__ __forceinline__ int stage_duals(const TiledArgs<T>& a, FlowSmem<T, B>& sm, const T* zb, int gtid) {
+  using C = TileCfg<B>;
+  using M = MaskCfg<B>;
+  constexpr int NWG = NTHG / 32;
+  constexpr int CH = (M::PER_BT + NTHG - 1) / NTHG;
+  const int lane = gtid & 31, gw = gtid >> 5;
+  int cnt = 0;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int q = gtid * CH + c;
+    if (q < M::PER_BT) cnt += __popc(sm.mask[q]);
+  }
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) sm.scan[gw] = incl;
+  group_sync<NTHG, NAMED>();
+  if (gw == 0) {
+    int v = lane < NWG ? sm.scan[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (lane < NWG) sm.scan[lane] = v;
+  }
+  group_sync<NTHG, NAMED>();
+  int run = (gw ? sm.scan[gw - 1] : 0) + incl - cnt;
+  const int total = sm.scan[NWG - 1];
+  if (gtid == 0) sm.total = total;
+  const bool staged = total <= M::CAP;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int q = gtid * CH + c;
+    if (q < M::PER_BT) {
+      uint32_t bits = sm.mask[q];
+      sm.pre[q] = run;
+      if (a.sparse) sm.nmask[q] = bits;
+      if (staged && bits && !a.sparse) {
+        const int t = q / (3 * M::WPR), r = (q / M::WPR) % 3, wd = q % M::WPR;
+        const T* src = zb + (int64_t)t * (3 * C::BB) + r * C::BB + wd * 32;
+        int idx = run;
+        while (bits) {
+          const int l = __ffs(bits) - 1;
+          bits &= bits - 1;
+          cp_async_ca<sizeof(T)>(&sm.dual[idx++], src + l);
+        }
+      }
+      run += __popc(sm.mask[q]);
+    }
+  }
+  return total;
+}
+
+// While warp 0 waits for block triple w's tiles, warps 1.. stage what the
+// item owns alone (its nonzero-dual bits, their prefix and its nonzero duals
+// of the dense store: written only by this item's visit of the previous
+// sweep), so that after the wait only the x tiles remain to be loaded.
+// Returns with the dual copies complete for the calling thread; a CTA
+// barrier must follow before other threads read them.
+template <typename T, int B, int NT>
+__device__ __noinline__ void prestage_item(const TiledArgs<T>& a, int w, FlowSmem<T, B>& sm) {
+  using C = TileCfg<B>;
+  using M = MaskCfg<B>;
+  constexpr int NTHG = NT - 32;
+  const int gtid = (int)threadIdx.x - 32;
+  const uint32_t* mb = a.mask + (int64_t)w * M::PER_BT;
+  const T* zb = a.zt + (int64_t)w * (3 * B * C::BB);
+  constexpr int MCH = M::PER_BT * 4 / 16;
+  for (int e = gtid; e < MCH; e += NTHG)
+    cp_async16(reinterpret_cast<char*>(sm.mask) + 16 * e, reinterpret_cast<const char*>(mb) + 16 * e);
+  cp_async_wait_all();
+  group_sync<NTHG, true>();
+  stage_duals<T, B, NTHG, true>(a, sm, zb, gtid);
+  cp_async_wait_all();
+}
+
 // The B sub-phases of one staged block triple.  FULL: I < J < K and no
 // ragged block, so every slot is a triplet and the thread owns its x_ij
 // (tile (I,J) entry (a,b) is touched only by slot (a,b)): x_ij and its float
@@ -708,7 +805,7 @@ __device__ __forceinline__ int flow_subphases_compact(const TiledArgs<T>& a, Flo
 // the B sub-phases.
 template <typename T, bool UNITW, int B, int NTH_>
 __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, int I, int J, int K,
-                                                  FlowSmem<T, B>& sm) {
+                                                  FlowSmem<T, B>& sm, bool prestaged = false) {
   using C = TileCfg<B>;
   using M = MaskCfg<B>;
   constexpr bool SHADOW = sizeof(T) == 8;
@@ -772,8 +869,9 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
   }
   constexpr int MCH = M::PER_BT * 4 / 16;
   if (!a.sparse) {
-    for (int e = tid; e < MCH; e += NTH)
-      cp_async16(reinterpret_cast<char*>(sm.mask) + 16 * e, reinterpret_cast<const char*>(mb) + 16 * e);
+    if (!prestaged)
+      for (int e = tid; e < MCH; e += NTH)
+        cp_async16(reinterpret_cast<char*>(sm.mask) + 16 * e, reinterpret_cast<const char*>(mb) + 16 * e);
   } else {
     // entries: set the bit, place the value in the CTA's scratch block and,
     // when they fit, in the staging array (ascending index = bit order)
@@ -797,56 +895,11 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
   cp_async_wait_all();
   item_sync<WARP>();
 
-  // exclusive prefix of the mask popcounts (the staging slot of each nonzero dual)
-  constexpr int CH = (M::PER_BT + NTH - 1) / NTH;
-  int cnt = 0;
-#pragma unroll
-  for (int c = 0; c < CH; ++c) {
-    const int q = tid * CH + c;
-    if (q < M::PER_BT) cnt += __popc(sm.mask[q]);
-  }
-  int incl = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int v = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += v;
-  }
-  if (lane == 31) sm.scan[wid] = incl;
-  item_sync<WARP>();
-  if (wid == 0) {
-    int v = lane < NW ? sm.scan[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int u = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += u;
-    }
-    if (lane < NW) sm.scan[lane] = v;
-  }
-  item_sync<WARP>();
-  int run = (wid ? sm.scan[wid - 1] : 0) + incl - cnt;
-  const int total = sm.scan[NW - 1];
-  if (tid == 0) sm.total = total;
+  // exclusive prefix of the mask popcounts (the staging slot of each nonzero
+  // dual) and the staging copies, unless warps 1.. did this during the wait
+  const int total = prestaged ? sm.total : stage_duals<T, B, NTH, false>(a, sm, zb, tid);
   const bool staged = total <= M::CAP;
-#pragma unroll
-  for (int c = 0; c < CH; ++c) {
-    const int q = tid * CH + c;
-    if (q < M::PER_BT) {
-      uint32_t bits = sm.mask[q];
-      sm.pre[q] = run;
-      if (a.sparse) sm.nmask[q] = bits;
-      if (staged && bits && !a.sparse) {
-        const int t = q / (3 * M::WPR), r = (q / M::WPR) % 3, wd = q % M::WPR;
-        const T* src = zb + (int64_t)t * (3 * C::BB) + r * C::BB + wd * 32;
-        int idx = run;
-        while (bits) {
-          const int l = __ffs(bits) - 1;
-          bits &= bits - 1;
-          cp_async_ca<sizeof(T)>(&sm.dual[idx++], src + l);
-        }
-      }
-      run += __popc(sm.mask[q]);
-    }
-  }
+  constexpr int CH = (M::PER_BT + NTH - 1) / NTH;
   if constexpr (SHADOW) {
     for (int e = tid; e < C::BB; e += NTH) {
       sm.f[0][e] = f32_trunc(sm.x[0][e]);
@@ -1044,29 +1097,31 @@ __global__ void __launch_bounds__(NT) k_sweep_flow(TiledArgs<T> a, int* flow) {
       const int g = (I + J + K) % a.nb;
       const int64_t tIJ = tile_index(a.nb, I, J), tIK = tile_index(a.nb, I, K), tJK = tile_index(a.nb, J, K);
       const int64_t u1 = (K == J) ? -1 : tIK, u2 = (I == J) ? -1 : tJK;
-      if constexpr (sizeof(T) == 8) {
-        // FP64 state (measured: about 1 % shorter sweeps; FP32 state, whose
-        // items wait less, was 1 % slower with it and waits plainly)
-        if (threadIdx.x == 0) {
-          const bool rdy = tiles_ready(tile_cnt, tIJ, u1, u2, g);
-          if (rdy) asm volatile("fence.acq_rel.gpu;" ::: "memory");
-          sm.ready = rdy;
-          sm.flag = rdy;
+      // one look at the tiles; if they are not ready, warp 0 waits while the
+      // other warps stage what the item owns alone (dense store: its bits,
+      // their prefix and its nonzero duals) or, for the sparse store in FP64
+      // state, bring its entry list toward L2
+      if (threadIdx.x == 0) {
+        const bool rdy = tiles_ready(tile_cnt, tIJ, u1, u2, g);
+        if (rdy) asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        sm.ready = rdy;
+        sm.flag = rdy;
+      }
+      __syncthreads();
+      bool pre = false;
+      if (!sm.ready) {
+        if (threadIdx.x >= 32) {
+          if (!a.sparse) prestage_item<T, B, NT>(a, w, sm);
+          else if (sizeof(T) == 8) warm_item<T, B>(a, w, (int)threadIdx.x - 32, NT - 32);
+        } else if (threadIdx.x == 0) {
+          sm.flag = wait_tiles(tile_cnt, tIJ, u1, u2, g, a.ctl, a.timeout_ns, g);
         }
         __syncthreads();
-        if (!sm.ready) {
-          // not ready: warp 0 waits while the other warps warm L2 for the staging
-          if (threadIdx.x >= 32) warm_item<T, B>(a, w, (int)threadIdx.x - 32, NT - 32);
-          else if (threadIdx.x == 0) sm.flag = wait_tiles(tile_cnt, tIJ, u1, u2, g, a.ctl, a.timeout_ns, g);
-          __syncthreads();
-        }
-      } else {
-        if (threadIdx.x == 0) sm.flag = wait_tiles(tile_cnt, tIJ, u1, u2, g, a.ctl, a.timeout_ns, g);
-        __syncthreads();
+        pre = !a.sparse;
       }
       if (tr && threadIdx.x == 0) tr[1] = global_ns();
       if (!sm.flag) return;
-      flow_block_triple<T, UNITW, B, NT>(a, w, I, J, K, sm);
+      flow_block_triple<T, UNITW, B, NT>(a, w, I, J, K, sm, pre);
       if (tr && threadIdx.x == 0) {
         tr[2] = global_ns();
         tr[4] = (unsigned long long)min(sm.total, 0xffffff) | ((unsigned long long)min(sm.ntrip, 0xffff) << 24) |
@@ -1228,11 +1283,15 @@ struct SumOp {
 
 // Largest metric-row violation max(0, x_h - x_a - x_b) over all triplets,
 // evaluated in FP64; one partial maximum per CTA.  A row is evaluated in FP64
-// only when its float estimate can still exceed the running maximum m: with
-// S = |x_h| + |x_a| + |x_b| the float delta is within 3.1 * 2^-24 S of the
-// double one, and skipping rows with RN(delta_f + 2 tau) <= m_f (tau =
-// 2^-21 S + 2^-100, m_f = m rounded down to float) never skips a row above m.
-// The maximum is order-free, so the result equals a serial FP64 evaluation.
+// only when its float estimate can still exceed the running maximum m.  The
+// float copies of FP64 state are truncated with integer operations
+// (f32_trunc, within 2^-23 |x|; a conversion instruction would occupy the
+// FP64 unit); with S = |x_h| + |x_a| + |x_b| the float delta is then within
+// 4.1 * 2^-24 S + 2^-124 of the double one, and skipping rows with
+// RN(delta_f + 2 tau) <= m_f (tau = 2^-21 S + 2^-100, m_f = m rounded down
+// to float) never skips a row above m: either S >= m / 11.9, and the margin
+// 2 tau - 4.1 * 2^-24 S covers m_f's half ulp, or delta <= S < m.  The
+// maximum is order-free, so the result equals a serial FP64 evaluation.
 template <typename T, int B>
 __global__ void __launch_bounds__(TileCfg<B>::NT) k_maxviol_tiled(const T* __restrict__ x, int n, int nb,
                                                                    const btpk* __restrict__ bt_list, int nbt,
@@ -1253,9 +1312,9 @@ __global__ void __launch_bounds__(TileCfg<B>::NT) k_maxviol_tiled(const T* __res
       sx[0][e] = v0;
       sx[1][e] = v1;
       sx[2][e] = v2;
-      sf[0][e] = (float)v0;
-      sf[1][e] = (float)v1;
-      sf[2][e] = (float)v2;
+      sf[0][e] = to_shadow(v0);
+      sf[1][e] = to_shadow(v1);
+      sf[2][e] = to_shadow(v2);
     }
     __syncthreads();
     const bool kj = (K == J), ij = (I == J);

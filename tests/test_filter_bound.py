@@ -132,3 +132,44 @@ def test_row_filter_is_sound_and_the_skipped_row_is_a_no_op():
                 assert np.all(np.maximum(zn, 0.0) == 0.0)
                 hits += ok.sum()
         assert hits > 0
+
+
+def _check_skips(f, m):
+    """The convergence check's skip rule (k_maxviol_tiled): a triplet's rows
+    are left out of the FP64 evaluation when RN(delta_f + 2 tau) <= m_f for
+    all three float row deltas, tau = RN(S 2^-21 + 2^-100), m_f = m rounded
+    down to float."""
+    S = (np.abs(f[:, 0]) + np.abs(f[:, 1])) + np.abs(f[:, 2])
+    tau2 = np.float32(2.0) * _fma32(S, np.float32(2.0 ** -21) * np.ones_like(S),
+                                    np.float32(2.0 ** -100) * np.ones_like(S))
+    mf = m.astype(np.float32)
+    mf = np.where(mf.astype(np.float64) > m, np.nextafter(mf, np.float32(-np.inf)), mf)   # round down
+    d0 = (f[:, 0] - f[:, 1]) - f[:, 2]
+    d1 = (f[:, 1] - f[:, 0]) - f[:, 2]
+    d2 = (f[:, 2] - f[:, 0]) - f[:, 1]
+    return (d0 + tau2 <= mf) & (d1 + tau2 <= mf) & (d2 + tau2 <= mf)
+
+
+def test_check_skip_rule_never_hides_a_row_above_the_running_maximum():
+    """With truncated (or rounded) float copies of double x, a skipped
+    triplet's exact double row deltas never exceed the running maximum m:
+    the check's maximum equals a serial FP64 evaluation over all rows."""
+    rng = np.random.default_rng(11)
+    for copy in (f32_trunc, lambda v: v.astype(np.float32)):
+        skipped = 0
+        for _ in range(10):
+            x = _cases(rng, 200000)
+            d0 = (x[:, 0] - x[:, 1]) - x[:, 2]
+            d1 = (x[:, 1] - x[:, 0]) - x[:, 2]
+            d2 = (x[:, 2] - x[:, 0]) - x[:, 1]
+            exact = np.maximum(np.maximum(d0, d1), d2)
+            # running maxima just above, at and below each triplet's own
+            # largest delta, and unrelated ones of other magnitudes
+            for m in (exact * (1 + 1e-7), exact, exact * (1 - 1e-7), np.abs(exact) + 1e-9,
+                      rng.choice([0.0, 1e-12, 1e-6, 1e-3, 1.0], exact.size)):
+                m = np.maximum(m, 0.0)
+                f = copy(x.ravel()).reshape(x.shape)
+                skip = _check_skips(f, m)
+                assert np.all(exact[skip] <= m[skip])
+                skipped += int(skip.sum())
+        assert skipped > 0
