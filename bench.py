@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--tile", type=int, default=16)
     p.add_argument("--precision", default="fp64", choices=["fp64", "fp32_refine"])
     p.add_argument("--check-every", type=int, default=10)
-    p.add_argument("--variant", type=int, default=0)
+    p.add_argument("--variant", type=int, default=-1, help="sweep form (-1: chosen per instance)")
     p.add_argument("--store", default="dense", choices=["dense", "sparse"])
     p.add_argument("--schedule", default="tiled", choices=["tiled", "summod", "diagonal"])
     p.add_argument("--grid", type=int, default=0)

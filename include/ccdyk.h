@@ -104,14 +104,19 @@ typedef struct cc_opts {
   int32_t debug_skip_cta;   /* test hook: this CTA skips its first barrier
                                arrival (-1 = off); the sweep then ends with
                                CC_ERR_TIMEOUT */
-  int32_t variant;          /* fused-form sweep kernel: 0 = one CTA per block
-                               triple (default); 1 = the same with compacted
+  int32_t variant;          /* fused-form sweep kernel: -1 = chosen per
+                               instance and precision (default): 3 when a
+                               phase holds at least twice as many block
+                               triples as form 0 keeps resident and form 3
+                               keeps more resident, else 0; 0 = one CTA per
+                               block triple; 1 = the same with compacted
                                update lists in FP64 state; 2 = one warp per
                                block triple (tile <= 16); 3 = one half-size
                                CTA per block triple (tile >= 16); 4 = as 0
                                with the float filters off (every triplet and
                                row updated: the reference the filtered forms
-                               equal in value).  All give the same values. */
+                               equal in value).  All give the same values.
+                               Batches run form 0 or 1 (cc_batch_autotune). */
   double refine_at;         /* CC_PREC_FP32_REFINE: cc_solve leaves FP32 when
                                the violation is <= a = max(tol, refine_at),
                                or is <= 100 a and stops decreasing between
@@ -153,8 +158,8 @@ typedef struct cc_opts {
                                block triple a list of its nonzero duals
                                (local index, value) in visiting order, so
                                memory is O(n^2 + nonzero duals).  Needs the
-                               tiled schedule, fused form and variant 0, 3
-                               or 4 (FP64 or the FP32 bulk form); duals can
+                               tiled schedule, fused form and variant -1, 0,
+                               3 or 4 (FP64 or the FP32 bulk form); duals can
                                be read (cc_get_duals)
                                but not set (cc_set_state, cc_set_duals,
                                warm start: CC_ERR_UNSUPPORTED); no batches.
@@ -192,6 +197,8 @@ typedef struct cc_stats {
                               the current pool); -1 with the dense store */
   int64_t pool_retries;    /* sparse store: sweeps undone and run again after
                               the next pool grew */
+  int32_t variant;         /* sweep form in use for the current precision
+                              (opts.variant, or the automatic choice) */
 } cc_stats;
 
 typedef struct cc_handle cc_handle;

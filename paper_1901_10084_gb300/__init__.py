@@ -80,7 +80,7 @@ class Solver:
 
     def __init__(self, n, d, w, eps=0.2, schedule="tiled", tile=16, precision="fp64",
                  exact=False, check_every=10, device=0, stream=None, torch_alloc=True,
-                 barrier_timeout_s=2.0, grid=0, debug_skip_cta=-1, on_device=False, variant=0,
+                 barrier_timeout_s=2.0, grid=0, debug_skip_cta=-1, on_device=False, variant=-1,
                  refine_at=1e-5, trace=False, interleave=True, problem="cc", store="dense",
                  pool_entries=0, refine_sweeps=5):
         o = cc_opts_default()

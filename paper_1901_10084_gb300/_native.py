@@ -83,6 +83,7 @@ class cc_stats(ctypes.Structure):
         ("state_fp32", ctypes.c_int32),
         ("dual_nnz", ctypes.c_int64),
         ("pool_retries", ctypes.c_int64),
+        ("variant", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:

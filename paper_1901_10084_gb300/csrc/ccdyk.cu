@@ -47,6 +47,7 @@ struct cc_handle {
   double* winv64 = nullptr;
   int64_t fp32_sweeps = 0;
   int64_t fp64_from = -1;   // sweep count when the state left FP32 (-1: never in this state)
+  int var = 0;               // sweep form in use (opts.variant, or the automatic choice)
   void* zt = nullptr;
   void* zp = nullptr;
   int64_t tile_elems = 0;   // ntiles * B * B
@@ -184,12 +185,12 @@ int warps_per_cta(int B) { return B == 8 ? 8 : 4; }
 // B >= 16, so that twice as many block triples are in flight per SM)
 int flow_threads(const cc_handle* h) {
   const int full = threads_for_tile(h->B);
-  return (h->o.variant == 3 && h->B >= 16) ? full / 2 : full;
+  return (h->var == 3 && h->B >= 16) ? full / 2 : full;
 }
 
 bool use_warp_kernel(const cc_handle* h) {
   if (h->o.exact || h->B > 16) return false;
-  return h->o.variant == 2;
+  return h->var == 2;
 }
 
 template <typename T, bool UNITW>
@@ -253,8 +254,8 @@ TiledArgs<T> tiled_args(cc_handle* h) {
   a.nbt = h->nbt;
   a.trace = h->trace;
   a.pairs = h->o.problem == CC_PROB_CC ? 1 : 0;
-  a.compact = h->o.variant == 1 ? 1 : 0;
-  a.nofilter = h->o.variant == 4 ? 1 : 0;
+  a.compact = h->var == 1 ? 1 : 0;
+  a.nofilter = h->var == 4 ? 1 : 0;
   a.sparse = h->sparse ? 1 : 0;
   a.zt_elems = (long long)h->zt_elems;
   a.mask_words = (long long)h->mask_words;
@@ -289,7 +290,50 @@ TiledArgs<T> tiled_args(cc_handle* h) {
   return a;
 }
 
+// CTAs of the dataflow sweep that stay resident: per-SM occupancy of the
+// kernel (at most 8) times the SMs.
+int resident_ctas(cc_handle* h, void* k, int threads, size_t smem, int* out) {
+  if (smem) CK(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem));
+  *out = std::min(per_sm, 8) * h->sms;
+  return CC_OK;
+}
+
+// opts.variant < 0: the sweep form for this instance and precision.  While a
+// phase holds about as many block triples as there are resident CTAs, the
+// sweep is paced by the chain of dependent items on each tile, and full-size
+// CTAs walk each item fastest (form 0).  When a phase holds at least twice
+// as many block triples as form 0 keeps resident, the CTAs are busy with
+// items more than they wait, so the form that keeps more CTAs resident wins:
+// half-size CTAs (form 3), if more of them fit.  Measured with the Chung-Lu
+// instances: n = 1000 form 0 (form 3 11 % slower); n = 2000 form 3 6 % faster
+// in FP64, 12 % in FP32; n = 3000 weighted: FP32 21 % faster with form 3, FP64
+// form 0 (the weighted half-size FP64 kernel holds no more CTAs).
+int choose_variant(cc_handle* h) {
+  h->var = 0;
+  if (h->o.exact || h->o.schedule != CC_SCHED_TILED || h->B < 16) return CC_OK;
+  const size_t smem = flow_smem(h->fp32, h->B);
+  const int full = threads_for_tile(h->B);
+  int slots0 = 0, slots3 = 0;
+  void* k0 = h->fp32 ? (h->unitw ? filtered_kernel_b<float, true>(h->B, false, false)
+                                 : filtered_kernel_b<float, false>(h->B, false, false))
+                     : (h->unitw ? filtered_kernel_b<double, true>(h->B, false, false)
+                                 : filtered_kernel_b<double, false>(h->B, false, false));
+  void* k3 = h->fp32 ? (h->unitw ? filtered_kernel_b<float, true>(h->B, false, true)
+                                 : filtered_kernel_b<float, false>(h->B, false, true))
+                     : (h->unitw ? filtered_kernel_b<double, true>(h->B, false, true)
+                                 : filtered_kernel_b<double, false>(h->B, false, true));
+  int rc = resident_ctas(h, k0, full, smem, &slots0);
+  if (rc) return rc;
+  rc = resident_ctas(h, k3, full / 2, smem, &slots3);
+  if (rc) return rc;
+  if ((int64_t)h->max_bt_phase >= 2 * (int64_t)slots0 && slots3 > slots0) h->var = 3;
+  return CC_OK;
+}
+
 int configure_sweep(cc_handle* h) {
+  h->var = h->o.variant < 0 ? 0 : h->o.variant;
   void* k = sweep_kernel(h);
   if (h->o.schedule != CC_SCHED_TILED) {
     int per_sm = 0;
@@ -302,6 +346,11 @@ int configure_sweep(cc_handle* h) {
     h->sweep_threads = 256;
     h->dyn_smem = 0;
     return CC_OK;
+  }
+  if (h->o.variant < 0) {
+    int rc = choose_variant(h);
+    if (rc) return rc;
+    k = sweep_kernel(h);
   }
   const bool wk = use_warp_kernel(h);
   const int threads = wk ? 32 * warps_per_cta(h->B) : flow_threads(h);
@@ -778,7 +827,7 @@ int check_opts(const cc_opts& o) {
   if (o.precision == CC_PREC_FP32_REFINE && o.schedule != CC_SCHED_TILED)
     return fail(nullptr, CC_ERR_ARG, "the FP32 bulk form runs on the tiled schedule");
   if (o.check_every < 1) return fail(nullptr, CC_ERR_ARG, "check_every must be >= 1");
-  if (o.variant < 0 || o.variant > 4) return fail(nullptr, CC_ERR_ARG, "variant must be 0..4");
+  if (o.variant < -1 || o.variant > 4) return fail(nullptr, CC_ERR_ARG, "variant must be -1 (automatic) or 0..4");
   if (!(o.barrier_timeout_s > 0.0)) return fail(nullptr, CC_ERR_ARG, "barrier_timeout_s must be > 0");
   if ((o.alloc == nullptr) != (o.free == nullptr)) return fail(nullptr, CC_ERR_ARG, "alloc and free go together");
   if (o.problem != CC_PROB_CC && o.problem != CC_PROB_L2) return fail(nullptr, CC_ERR_ARG, "unknown problem");
@@ -788,8 +837,8 @@ int check_opts(const cc_opts& o) {
   if (o.pool_entries < 0) return fail(nullptr, CC_ERR_ARG, "pool_entries must be >= 0");
   if (o.refine_sweeps < 1) return fail(nullptr, CC_ERR_ARG, "refine_sweeps must be >= 1");
   if (o.store == CC_STORE_SPARSE &&
-      (o.schedule != CC_SCHED_TILED || o.exact || (o.variant != 0 && o.variant != 3 && o.variant != 4)))
-    return fail(nullptr, CC_ERR_UNSUPPORTED, "the sparse store runs the tiled schedule, fused form, variant 0, 3 or 4");
+      (o.schedule != CC_SCHED_TILED || o.exact || (o.variant != -1 && o.variant != 0 && o.variant != 3 && o.variant != 4)))
+    return fail(nullptr, CC_ERR_UNSUPPORTED, "the sparse store runs the tiled schedule, fused form, variant -1, 0, 3 or 4");
   return CC_OK;
 }
 
@@ -945,7 +994,7 @@ void cc_opts_default(cc_opts* o) {
   o->alloc_ctx = nullptr;
   o->grid = 0;
   o->debug_skip_cta = -1;
-  o->variant = 0;
+  o->variant = -1;
   o->refine_at = 1e-5;
   o->trace = 0;
   o->interleave = 1;
@@ -1107,6 +1156,7 @@ void check_finish(cc_handle* h, cc_stats* st) {
   s.fp32_sweeps = h->fp32_sweeps;
   s.dual_nnz = h->sparse ? h->sp_nnz : -1;
   s.pool_retries = h->sp_retries;
+  s.variant = h->var;
   s.state_fp32 = h->fp32 ? 1 : 0;
   s.max_violation = mv;
   s.pair_violation = pv;
@@ -1388,6 +1438,7 @@ int cc_get_stats(cc_handle* h, cc_stats* st) {
   st->state_fp32 = h->fp32 ? 1 : 0;
   st->dual_nnz = h->sparse ? h->sp_nnz : -1;
   st->pool_retries = h->sp_retries;
+  st->variant = h->var;
   return CC_OK;
 }
 

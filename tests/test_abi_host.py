@@ -37,13 +37,13 @@ def test_opts_defaults(lib):
     o = N.cc_opts_default()
     assert o.eps == 0.2 and o.schedule == N.CC_SCHED_TILED and o.tile == 16
     assert o.precision == N.CC_PREC_FP64 and o.check_every == 10 and o.debug_skip_cta == -1
-    assert o.refine_sweeps == 5 and o.refine_at == 1e-5
+    assert o.refine_sweeps == 5 and o.refine_at == 1e-5 and o.variant == -1
 
 
 @pytest.mark.parametrize("field,value", [("eps", 0.0), ("eps", -1.0), ("eps", float("inf")),
                                          ("tile", 12), ("check_every", 0),
                                          ("barrier_timeout_s", 0.0), ("precision", 7), ("variant", 5),
-                                         ("variant", -1), ("refine_sweeps", 0), ("refine_sweeps", -3)])
+                                         ("variant", -2), ("refine_sweeps", 0), ("refine_sweeps", -3)])
 def test_bad_options_rejected_before_device_work(lib, field, value):
     import numpy as np
     from paper_1901_10084_gb300 import _native as N

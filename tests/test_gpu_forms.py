@@ -134,3 +134,28 @@ def test_random_configurations_equal_the_unfiltered_sweep():
         b = _run(n, d, w, sweeps, variant=4, **kw)
         for u, v in zip(a[:4], b[:4]):
             assert np.array_equal(u, v), (case, kw, n, sweeps)
+
+
+def test_automatic_sweep_form_gives_the_same_values():
+    """opts.variant = -1 (the default) picks form 0 or 3 per instance and
+    precision; the forms give the same values, so the automatic choice equals
+    form 0 bit for bit.  A small instance (one phase holds few block triples)
+    keeps form 0."""
+    import numpy as np
+    import paper_1901_10084_gb300 as cc
+    from instances import chung_lu
+    d, w, _ = chung_lu(90, 2.5, 8.0, seed=3)
+    with cc.Solver(90, d, w, tile=16) as s:
+        s.sweep(2)
+        assert s.stats()["variant"] == 0
+    n = 2000
+    d, w, _ = chung_lu(n, 2.5, 8.0, seed=4)
+    for prec in ("fp64", "fp32_refine"):
+        out = []
+        for v in (-1, 0):
+            with cc.Solver(n, d, w, tile=16, precision=prec, variant=v) as s:
+                s.sweep(4)
+                st = s.stats()
+                out.append((s.get_x()[0], st["variant"]))
+        assert out[0][1] in (0, 3) and out[1][1] == 0
+        assert np.array_equal(out[0][0], out[1][0])
