@@ -345,6 +345,7 @@ struct alignas(16) FlowSmem {
   int scan[32];
   int item, flag, total, dirty;
   int ready;                // the item's tiles were ready at the first look
+  int t0;                   // first sub-phase with an update (items without nonzero duals)
   uint32_t nmask[MaskCfg<B>::PER_BT];   // sparse store: nonzero-dual bits after the item
   unsigned long long base;              //   and its place in the next pool
   int ntrip, nrows, nsub;   // trace counters: triplets updated, rows executed, sub-phases with updates
@@ -580,7 +581,32 @@ __device__ __forceinline__ int flow_subphases(const TiledArgs<T>& a, int w, Flow
     }
   }
   int touched = 0;
-  for (int t = 0; t < B; ++t) {
+  int t_start = 0;
+  if constexpr (FULL && !HASMASK) {
+    // no nonzero dual: until the first sub-phase in which some triplet
+    // fails the filter nothing changes, so that sub-phase is found from the
+    // staged tiles in one pass without barriers, and the walk starts there
+    // (an item with no such sub-phase changes nothing at all)
+    if (!a.nofilter) {
+      // a thread stops at the first sub-phase it needs, or at one that some
+      // thread already found to need an update (the minimum only falls, and
+      // a thread stopping at t saw no need before t, so the minimum found is
+      // the first sub-phase with any need)
+      int first = B;
+      volatile int* t0v = &sm.t0;
+      for (int t = 0; t < B && first == B && t < *t0v; ++t) {
+#pragma unroll
+        for (int q = 0; q < SPT; ++q) {
+          const int lc = (t - la[q] - lb[q]) & (B - 1);
+          if (!inactive_fast(fr[q], gIK[la[q] * B + lc], gJK[lb[q] * B + lc])) first = t;
+        }
+      }
+      if (first < B) atomicMin(&sm.t0, first);
+      item_sync<WARP>();
+      t_start = sm.t0;
+    }
+  }
+  for (int t = t_start; t < B; ++t) {
     T* zs = zb + (int64_t)t * (3 * C::BB);
     const int qt = t * (3 * M::WPR);
 #pragma unroll
@@ -887,6 +913,7 @@ __device__ __forceinline__ void flow_block_triple(const TiledArgs<T>& a, int w, 
   for (int e = tid; e < B; e += NTH) sm.lcnt[e] = 0;
   if (tid == 0) {
     sm.dirty = 0;
+    sm.t0 = B;
     sm.ntrip = 0;
     sm.nrows = 0;
     sm.nsub = 0;
@@ -1282,41 +1309,67 @@ struct SumOp {
 };
 
 // Largest metric-row violation max(0, x_h - x_a - x_b) over all triplets,
-// evaluated in FP64; one partial maximum per CTA.  A row is evaluated in FP64
-// only when its float estimate can still exceed the running maximum m.  The
-// float copies of FP64 state are truncated with integer operations
-// (f32_trunc, within 2^-23 |x|; a conversion instruction would occupy the
-// FP64 unit); with S = |x_h| + |x_a| + |x_b| the float delta is then within
-// 4.1 * 2^-24 S + 2^-124 of the double one, and skipping rows with
-// RN(delta_f + 2 tau) <= m_f (tau = 2^-21 S + 2^-100, m_f = m rounded down
-// to float) never skips a row above m: either S >= m / 11.9, and the margin
-// 2 tau - 4.1 * 2^-24 S covers m_f's half ulp, or delta <= S < m.  The
-// maximum is order-free, so the result equals a serial FP64 evaluation.
+// evaluated in FP64; one partial maximum per CTA.  A triplet's rows are
+// evaluated in FP64 only when their float estimate can still exceed the
+// running maximum m.  The largest row delta of a triplet is 2 max(x) - sum(x);
+// from float copies of its three values (for FP64 state truncated with
+// integer operations, f32_trunc: within 2^-23 |x|; a conversion instruction
+// would occupy the FP64 unit) that estimate is within 11 * 2^-24 S + 2^-123
+// of the exact one (S = |x_h| + |x_a| + |x_b|; three copies, two additions,
+// one fused multiply-add).  Skipping when RN(dmax_f + tau) <= m_f (tau =
+// RN(2^-19 S + 2^-100), m_f = m rounded down to float) never skips a row
+// above m: either S >= m / 21, and the margin tau - 11 * 2^-24 S covers m_f's
+// half ulp, or every row delta <= S < m.  The maximum is order-free, so the
+// result equals a serial FP64 evaluation.  Each CTA walks block triples with
+// the next one's three tiles already on their way (asynchronous copies into
+// a second buffer).
 template <typename T, int B>
 __global__ void __launch_bounds__(TileCfg<B>::NT) k_maxviol_tiled(const T* __restrict__ x, int n, int nb,
                                                                    const btpk* __restrict__ bt_list, int nbt,
                                                                    double* part) {
   using C = TileCfg<B>;
-  __shared__ T sx[3][C::BB];
+  // two tile buffers where they fit in the 48 KB of static shared memory
+  constexpr int NBUF = (3 * C::BB * (int)sizeof(T) * 2 + 3 * C::BB * 4 <= 40 * 1024) ? 2 : 1;
+  __shared__ __align__(16) T sx[NBUF][3][C::BB];
   __shared__ float sf[3][C::BB];
   __shared__ double sred[32];
+  constexpr int XCH = C::BB * (int)sizeof(T) / 16;     // 16-byte chunks per tile
   double m = 0.0;
   float mf = 0.0f;
-  for (int w = blockIdx.x; w < nbt; w += gridDim.x) {
+  auto issue = [&](int w, int buf) {
     int I, J, K;
     unpack_bt(bt_list[w], I, J, K);
-    const int64_t oIJ = tile_index(nb, I, J) * C::BB, oIK = tile_index(nb, I, K) * C::BB,
-                  oJK = tile_index(nb, J, K) * C::BB;
-    for (int e = threadIdx.x; e < C::BB; e += C::NT) {
-      const T v0 = x[oIJ + e], v1 = x[oIK + e], v2 = x[oJK + e];
-      sx[0][e] = v0;
-      sx[1][e] = v1;
-      sx[2][e] = v2;
-      sf[0][e] = to_shadow(v0);
-      sf[1][e] = to_shadow(v1);
-      sf[2][e] = to_shadow(v2);
+    const int64_t o0 = tile_index(nb, I, J) * C::BB, o1 = tile_index(nb, I, K) * C::BB,
+                  o2 = tile_index(nb, J, K) * C::BB;
+    for (int e = threadIdx.x; e < 3 * XCH; e += C::NT) {
+      const int t = e / XCH, c = e % XCH;
+      const int64_t ot = t == 0 ? o0 : (t == 1 ? o1 : o2);
+      cp_async16(reinterpret_cast<char*>(sx[buf][t]) + 16 * c, reinterpret_cast<const char*>(x + ot) + 16 * c);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  int buf = 0;
+  if (NBUF == 2 && (int)blockIdx.x < nbt) issue(blockIdx.x, 0);
+  for (int w = blockIdx.x; w < nbt; w += gridDim.x) {
+    const int wn = w + gridDim.x;
+    if (NBUF == 1) {
+      issue(w, 0);
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    } else if (wn < nbt) {
+      issue(wn, buf ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
     __syncthreads();
+    for (int e = threadIdx.x; e < C::BB; e += C::NT) {
+      sf[0][e] = to_shadow(sx[buf][0][e]);
+      sf[1][e] = to_shadow(sx[buf][1][e]);
+      sf[2][e] = to_shadow(sx[buf][2][e]);
+    }
+    __syncthreads();
+    int I, J, K;
+    unpack_bt(bt_list[w], I, J, K);
     const bool kj = (K == J), ij = (I == J);
     const int kB = K * B;
     for (int slot = threadIdx.x; slot < C::BB; slot += C::NT) {
@@ -1325,12 +1378,12 @@ __global__ void __launch_bounds__(TileCfg<B>::NT) k_maxviol_tiled(const T* __res
       const float fij = sf[0][la * B + lb];
       for (int lc = kj ? lb + 1 : 0; lc < B && kB + lc < n; ++lc) {
         const float fik = sf[1][la * B + lc], fjk = sf[2][lb * B + lc];
-        const float S = fabsf(fij) + fabsf(fik) + fabsf(fjk);
-        const float tau2 = 2.0f * fmaf(S, 0x1p-21f, 0x1p-100f);
-        const float d0 = (fij - fik) - fjk, d1 = (fik - fij) - fjk, d2 = (fjk - fij) - fik;
-        if (d0 + tau2 > mf || d1 + tau2 > mf || d2 + tau2 > mf) {
-          const double xij = (double)sx[0][la * B + lb];
-          const double xik = (double)sx[1][la * B + lc], xjk = (double)sx[2][lb * B + lc];
+        const float mx = fmaxf(fmaxf(fij, fik), fjk);
+        const float dmax = fmaf(2.0f, mx, -((fij + fik) + fjk));
+        const float S = (fabsf(fij) + fabsf(fik)) + fabsf(fjk);
+        if (dmax + fmaf(S, 0x1p-19f, 0x1p-100f) > mf) {
+          const double xij = (double)sx[buf][0][la * B + lb];
+          const double xik = (double)sx[buf][1][la * B + lc], xjk = (double)sx[buf][2][lb * B + lc];
           const double v0 = (xij - xik) - xjk, v1 = (xik - xij) - xjk, v2 = (xjk - xij) - xik;
           const double v = fmax(v0, fmax(v1, v2));
           if (v > m) {
@@ -1340,7 +1393,8 @@ __global__ void __launch_bounds__(TileCfg<B>::NT) k_maxviol_tiled(const T* __res
         }
       }
     }
-    __syncthreads();
+    __syncthreads();   // buffer buf is refilled two items on (one with a single buffer)
+    if (NBUF == 2) buf ^= 1;
   }
   m = block_reduce(m, MaxOp(), sred, 0.0);
   if (threadIdx.x == 0) part[blockIdx.x] = m;

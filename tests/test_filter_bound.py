@@ -136,18 +136,17 @@ def test_row_filter_is_sound_and_the_skipped_row_is_a_no_op():
 
 def _check_skips(f, m):
     """The convergence check's skip rule (k_maxviol_tiled): a triplet's rows
-    are left out of the FP64 evaluation when RN(delta_f + 2 tau) <= m_f for
-    all three float row deltas, tau = RN(S 2^-21 + 2^-100), m_f = m rounded
-    down to float."""
-    S = (np.abs(f[:, 0]) + np.abs(f[:, 1])) + np.abs(f[:, 2])
-    tau2 = np.float32(2.0) * _fma32(S, np.float32(2.0 ** -21) * np.ones_like(S),
-                                    np.float32(2.0 ** -100) * np.ones_like(S))
+    are left out of the FP64 evaluation when RN(dmax_f + tau) <= m_f, with
+    dmax_f = RN(2 max - sum) the float estimate of its largest row delta,
+    tau = RN(S 2^-19 + 2^-100), m_f = m rounded down to float."""
+    a, b, c = f[:, 0], f[:, 1], f[:, 2]
+    mx = np.maximum(np.maximum(a, b), c)
+    dmax = _fma32(np.float32(2.0) * np.ones_like(mx), mx, -((a + b) + c))
+    S = (np.abs(a) + np.abs(b)) + np.abs(c)
+    tau = _fma32(S, np.float32(2.0 ** -19) * np.ones_like(S), np.float32(2.0 ** -100) * np.ones_like(S))
     mf = m.astype(np.float32)
     mf = np.where(mf.astype(np.float64) > m, np.nextafter(mf, np.float32(-np.inf)), mf)   # round down
-    d0 = (f[:, 0] - f[:, 1]) - f[:, 2]
-    d1 = (f[:, 1] - f[:, 0]) - f[:, 2]
-    d2 = (f[:, 2] - f[:, 0]) - f[:, 1]
-    return (d0 + tau2 <= mf) & (d1 + tau2 <= mf) & (d2 + tau2 <= mf)
+    return dmax + tau <= mf
 
 
 def test_check_skip_rule_never_hides_a_row_above_the_running_maximum():
