@@ -1376,8 +1376,10 @@ __global__ void __launch_bounds__(TileCfg<B>::NT) k_maxviol_tiled(const T* __res
       const int la = slot / B, lb = slot % B;
       if (ij && la >= lb) continue;
       const float fij = sf[0][la * B + lb];
-      for (int lc = kj ? lb + 1 : 0; lc < B && kB + lc < n; ++lc) {
-        const float fik = sf[1][la * B + lc], fjk = sf[2][lb * B + lc];
+      const float* fik_row = sf[1] + la * B;
+      const float* fjk_row = sf[2] + lb * B;
+      auto triplet = [&](int lc) {
+        const float fik = fik_row[lc], fjk = fjk_row[lc];
         const float mx = fmaxf(fmaxf(fij, fik), fjk);
         const float dmax = fmaf(2.0f, mx, -((fij + fik) + fjk));
         const float S = (fabsf(fij) + fabsf(fik)) + fabsf(fjk);
@@ -1391,6 +1393,12 @@ __global__ void __launch_bounds__(TileCfg<B>::NT) k_maxviol_tiled(const T* __res
             mf = __double2float_rd(m);
           }
         }
+      };
+      if (!kj && kB + B <= n) {   // every c of the K block: an unrolled run
+#pragma unroll
+        for (int lc = 0; lc < B; ++lc) triplet(lc);
+      } else {
+        for (int lc = kj ? lb + 1 : 0; lc < B && kB + lc < n; ++lc) triplet(lc);
       }
     }
     __syncthreads();   // buffer buf is refilled two items on (one with a single buffer)
