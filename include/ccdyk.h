@@ -409,7 +409,8 @@ const char* cc_batch_last_error(const cc_batch* b);
  * the dense store (CC_ERR_UNSUPPORTED otherwise).  In the FP32 bulk phase of
  * CC_PREC_FP32_REFINE the same steps run on FP64 copies of the state and
  * the result is rounded to FP32.  Synchronous.  Errors:
- * CC_ERR_ARG, CC_ERR_UNSUPPORTED, CC_ERR_OOM, CC_ERR_CUDA. */
+ * CC_ERR_ARG, CC_ERR_UNSUPPORTED, CC_ERR_OOM (state unchanged), CC_ERR_CUDA
+ * (the state is then undefined). */
 int cc_warm_start_mlp(cc_handle* h, const float* params, double threshold, int64_t* candidates);
 
 /* Training samples of the handle's current state: feat (device, cap rows of

@@ -1924,7 +1924,10 @@ int cc_warm_start_mlp(cc_handle* h, const float* params, double threshold, int64
     return fail(h, CC_ERR_OOM, "parameters");
   }
   // FP32 bulk state: the same steps run on FP64 copies of the state, which
-  // are rounded to FP32 at the end (the bulk phase's precision)
+  // are rounded to FP32 at the end (the bulk phase's precision).  The FP32
+  // store is cleared through its bits first; the FP64 copy of the store is
+  // read and rounded only where the prediction leaves a bit set (the resync
+  // too reads only those slots), so it is never cleared as a whole
   const bool f32 = h->fp32;
   void* keep[6] = {h->zt, h->zp, h->x, h->f, h->d, h->winv};
   if (f32) {
@@ -1937,6 +1940,8 @@ int cc_warm_start_mlp(cc_handle* h, const float* params, double threshold, int64
       ws_release(h, c);
       return fail(h, CC_ERR_OOM, "FP64 warm-start state");
     }
+    k_ws_clear_by_mask<float><<<grid_for(h, h->mask_words, 256), 256, 0, h->st>>>(h->mask, (float*)keep[0],
+                                                                                h->mask_words);
     h->zt = t[0];
     h->zp = t[1];
     h->x = t[2];
@@ -1946,27 +1951,34 @@ int cc_warm_start_mlp(cc_handle* h, const float* params, double threshold, int64
     h->fp32 = false;
     h->esz = 8;
   }
-  // errors from here on fall through to the restore below
+  // errors from here on fall through to the restore below.  FP64 state:
+  // the store is cleared through its nonzero bits (the bits describe it
+  // exactly); in both states the inference sets the bits of what it writes,
+  // so neither a pass over the whole store nor a rebuild of the bits is
+  // needed
   cudaError_t ce = cudaMemcpyAsync(pd, params, WS_NPARAM * sizeof(float), cudaMemcpyHostToDevice, h->st);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(h->zt, 0, (size_t)h->zt_elems * sizeof(double), h->st);
+  if (ce == cudaSuccess && !f32) {
+    k_ws_clear_by_mask<double><<<grid_for(h, h->mask_words, 256), 256, 0, h->st>>>(h->mask, (double*)h->zt,
+                                                                                 h->mask_words);
+    ce = cudaGetLastError();
+  }
   if (ce == cudaSuccess) ce = cudaMemsetAsync(h->zp, 0, (size_t)h->tile_elems * 2 * sizeof(double), h->st);
   if (ce == cudaSuccess && c.count > 0) {
     const int grid = (int)std::min<int64_t>((c.count + 127) / 128, (int64_t)h->sms * 8);
     k_ws_infer<<<grid, 256, 0, h->st>>>(pd, c.feat, c.count, 1, nullptr, c.cand, (double*)h->zt, h->bt_rank, h->nb,
-                                        h->B, h->o.eps, (float)threshold);
+                                        h->B, h->o.eps, (float)threshold, h->mask);
   }
   if (ce == cudaSuccess) ce = cudaGetLastError();
   rc = ce == cudaSuccess ? CC_OK : fail(h, CC_ERR_CUDA, "warm-start inference");
-  if (rc == CC_OK) {
-    rebuild_mask(h, false);
-    rc = resync_fp64(h);
-  }
+  if (rc == CC_OK) rc = resync_fp64(h);
   if (rc == CC_OK) rc = cc_pair_passes(h, CC_WS_PAIR_PASSES);
   if (f32) {   // round to FP32, back to the FP32 arrays; bits from the rounded duals
     const size_t te = (size_t)h->tile_elems;
     if (rc == CC_OK) {
-      k_convert<double, float><<<grid_for(h, h->zt_elems, 256), 256, 0, h->st>>>((const double*)h->zt, (float*)keep[0],
-                                                                              h->zt_elems);
+      // a nonzero prediction is at least the smallest normal float over eps,
+      // so its rounding stays nonzero and the bits describe the FP32 store
+      k_ws_round_by_mask<<<grid_for(h, h->mask_words, 256), 256, 0, h->st>>>(h->mask, (const double*)h->zt,
+                                                                            (float*)keep[0], h->mask_words);
       k_convert<double, float><<<grid_for(h, 2 * te, 256), 256, 0, h->st>>>((const double*)h->zp, (float*)keep[1],
                                                                           2 * (int64_t)te);
       k_convert<double, float><<<grid_for(h, te, 256), 256, 0, h->st>>>((const double*)h->x, (float*)keep[2], te);
@@ -1985,7 +1997,10 @@ int cc_warm_start_mlp(cc_handle* h, const float* params, double threshold, int64
     h->winv = keep[5];
     h->fp32 = true;
     h->esz = 4;
-    rebuild_mask(h, true);   // also after a failure: the bits then describe the FP32 duals kept
+    if (rc != CC_OK) {   // after a failure the FP32 store may hold part of the prediction
+      CK(h, cudaMemsetAsync(h->zt, 0, (size_t)h->zt_elems * sizeof(float), h->st));
+      CK(h, cudaMemsetAsync(h->mask, 0, (size_t)h->mask_words * sizeof(uint32_t), h->st));
+    }
     const int r2 = cudaGetLastError() == cudaSuccess ? CC_OK : fail(h, CC_ERR_CUDA, "FP32 warm-start state");
     if (rc == CC_OK) rc = r2;
   }

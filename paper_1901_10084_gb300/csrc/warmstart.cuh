@@ -248,15 +248,48 @@ __device__ __forceinline__ int64_t tiled_dual_slot(const int* bt_rank, int nb, i
   return w * (3 * (int64_t)B * B * B) + (int64_t)t * (3 * B * B) + la * B + lb;
 }
 
+// Every dual whose nonzero bit is set back to zero, and the bits cleared: the
+// dense store all zero again after a pass over the bits alone (one thread
+// per mask word; bit b of word q is slot 32 q + b of the store).
+template <typename T>
+__global__ void k_ws_clear_by_mask(uint32_t* mask, T* zt, int64_t nwords) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nwords; q += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t bits = mask[q];
+    if (!bits) continue;
+    while (bits) {
+      const int l = __ffs(bits) - 1;
+      bits &= bits - 1;
+      zt[q * 32 + l] = T(0);
+    }
+    mask[q] = 0u;
+  }
+}
+
+// The duals whose bit is set rounded from an FP64 store into an FP32 store
+// (same layout); the other slots of the FP32 store are left as they are.
+__global__ void k_ws_round_by_mask(const uint32_t* __restrict__ mask, const double* __restrict__ z64, float* z32,
+                                   int64_t nwords) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nwords; q += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t bits = mask[q];
+    while (bits) {
+      const int l = __ffs(bits) - 1;
+      bits &= bits - 1;
+      z32[q * 32 + l] = (float)z64[q * 32 + l];
+    }
+  }
+}
+
 // ------------------------------------------------------------ inference
 
 // One warp per 16 candidates.  mode 0: out[3q + r] = softplus(mlp(feat_q))_r;
 // mode 1: the same values, below `threshold` set to 0, written as scaled duals
-// z = y / eps into the dual store (FP64) at the candidate's slots.
+// z = y / eps into the dual store (FP64) at the candidate's slots; with mask
+// non-null the nonzero-dual bit of every dual written nonzero is set (the
+// mask holds one bit per slot of the store, in the same order).
 __global__ void __launch_bounds__(256) k_ws_infer(const float* __restrict__ params, const float* __restrict__ feat,
                                                  int64_t count, int mode, float* out, const int64_t* __restrict__ cand,
                                                  double* zt, const int* __restrict__ bt_rank, int nb, int B,
-                                                 double eps, float threshold) {
+                                                 double eps, float threshold, uint32_t* mask = nullptr) {
   __shared__ WsSmem s;
   __shared__ float xs[8][16 * WS_FEAT];
   ws_stage_weights(params, s);
@@ -288,7 +321,9 @@ __global__ void __launch_bounds__(256) k_ws_infer(const float* __restrict__ para
           if (y < threshold) y = 0.f;
           const int64_t pk = cand[r];
           const int a = (int)(pk & 0x1fffff), b = (int)((pk >> 21) & 0x1fffff), c = (int)(pk >> 42);
-          zt[tiled_dual_slot(bt_rank, nb, B, a, b, c) + (int64_t)col * B * B] = (double)y / eps;
+          const int64_t gi = tiled_dual_slot(bt_rank, nb, B, a, b, c) + (int64_t)col * B * B;
+          zt[gi] = (double)y / eps;
+          if (mask && y > 0.f) atomicOr(mask + (gi >> 5), 1u << (gi & 31));
         }
       }
     }
