@@ -1891,19 +1891,6 @@ bool ws_usable(const cc_handle* h) {
   return h->o.schedule == CC_SCHED_TILED && !h->o.exact && h->mask && h->o.problem == CC_PROB_CC;
 }
 
-template <int B>
-void rebuild_mask(cc_handle* h, bool f32) {
-  const int g = grid_for(h, h->mask_words, 256);
-  if (f32) k_rebuild_mask<float, B><<<g, 256, 0, h->st>>>((const float*)h->zt, h->mask, h->mask_words);
-  else k_rebuild_mask<double, B><<<g, 256, 0, h->st>>>((const double*)h->zt, h->mask, h->mask_words);
-}
-
-void rebuild_mask(cc_handle* h, bool f32) {
-  if (h->B == 8) rebuild_mask<8>(h, f32);
-  else if (h->B == 16) rebuild_mask<16>(h, f32);
-  else rebuild_mask<32>(h, f32);
-}
-
 }  // namespace
 
 extern "C" {
