@@ -1183,9 +1183,14 @@ __global__ void __launch_bounds__(NT) k_sweep_flow(TiledArgs<T> a, int* flow) {
 // schedule order, then its pair tiles, and the list keeps every instance's
 // items in that order, so each item depends only on items listed before it
 // and the dataflow argument above carries over.  Instances are independent,
-// so the items of one fill the dependency waits of another.
+// so the items of one fill the dependency waits of another.  The arguments of
+// an item's instance are read from global memory, which costs registers the
+// single-instance kernel does not spend; for B = 16 the kernel is held to 64
+// registers so that four CTAs share an SM (80 registers gave three).  The
+// batch keeps the FP64 pipe busy (its instances keep many rows active), and
+// the fourth CTA outweighs the few spilled bytes the cap costs.
 template <typename T, bool UNITW, int B, int NT>
-__global__ void __launch_bounds__(NT) k_sweep_batch(const TiledArgs<T>* __restrict__ args,
+__global__ void __launch_bounds__(NT, (B == 16 && NT == 256) ? 4 : 1) k_sweep_batch(const TiledArgs<T>* __restrict__ args,
                                                     const int2* __restrict__ items, int total, int* next) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FlowSmem<T, B>& sm = *reinterpret_cast<FlowSmem<T, B>*>(smem_raw);
