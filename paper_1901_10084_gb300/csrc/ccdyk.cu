@@ -250,7 +250,6 @@ TiledArgs<T> tiled_args(cc_handle* h) {
   a.r_unit = (T)(1.0 / 3.0);
   a.skip_cta = h->o.debug_skip_cta;
   a.mask = h->mask;
-  a.work = nullptr;
   a.nbt = h->nbt;
   a.trace = h->trace;
   a.pairs = h->o.problem == CC_PROB_CC ? 1 : 0;

@@ -48,7 +48,6 @@ struct TiledArgs {
   T r_unit;             // 1/3: 1/(a^T W^{-1} a) for unit weights
   int skip_cta;         // fault-injection hook (-1 = off)
   uint32_t* mask;       // nonzero-dual bits, same schedule order as zt (filtered form)
-  int* work;            // unused
   int nbt;              // block triples per sweep
   unsigned long long* trace;  // optional per-item timestamps (nullptr = off)
   int* cnt;             // per-tile visit counters of this instance (batched sweep)
